@@ -1,0 +1,214 @@
+"""Seeded synthetic inputs for the dataflow graph (shared by tests and bench).
+
+This module holds no arithmetic of the method itself: it only draws the input
+stream, the FIR taps, the matrix H, the per-frame burst pattern and the
+per-instance thresholds of the workloads, deterministically from a seed.
+
+Generator: a counter-based hash, the SplitMix64 finaliser (Steele, Lea and
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) applied
+to ``key + (counter + 1) * 0x9E3779B97F4A7C15``, turned into a uniform double
+in (0, 1) from its top 53 bits, and into Gaussians by the Box-Muller
+transform in FP64, rounded to FP32 at the end.  Any frame of any instance can
+be regenerated on its own, on the CPU or on a CUDA device, from
+(seed, tag, instance, frame).
+
+Distribution conventions: CN(0, s2) has real and imaginary parts each
+N(0, s2 / 2); a "burst" block is the same draw with its amplitude scaled by 4
+(energy x16); a frame with burst fraction p has exactly round(p * F) burst
+blocks chosen without replacement (the blocks with the smallest per-block hash
+draws).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+MASK64 = (1 << 64) - 1
+GOLDEN = 0x9E3779B97F4A7C15
+_C1 = 0xBF58476D1CE4E5B9
+_C2 = 0x94D049BB133111EB
+
+TAG_X, TAG_TAPS, TAG_H, TAG_BURST, TAG_FRAC, TAG_TAU, TAG_SHAPE = 1, 2, 3, 4, 5, 6, 7
+
+
+def mix64(z: int) -> int:
+    """SplitMix64 finaliser on a Python int (mod 2^64)."""
+    z &= MASK64
+    z = ((z ^ (z >> 30)) * _C1) & MASK64
+    z = ((z ^ (z >> 27)) * _C2) & MASK64
+    return z ^ (z >> 31)
+
+
+def stream_key(seed: int, *ids: int) -> int:
+    """A 64-bit key for one named stream (tag, instance, frame ...)."""
+    k = mix64(seed + GOLDEN)
+    for i in ids:
+        k = mix64(k ^ mix64((i + 1) * GOLDEN))
+    return k
+
+
+def _s64(v: int) -> int:
+    """Reinterpret an unsigned 64-bit value as signed (torch int64)."""
+    v &= MASK64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _shr(z: torch.Tensor, k: int) -> torch.Tensor:
+    """Logical right shift of int64 lanes."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _mix64_t(z: torch.Tensor) -> torch.Tensor:
+    z = (z ^ _shr(z, 30)) * _s64(_C1)
+    z = (z ^ _shr(z, 27)) * _s64(_C2)
+    return z ^ _shr(z, 31)
+
+
+def uniform(key: int, start: int, n: int, device="cpu") -> torch.Tensor:
+    """Doubles in (0, 1): counters start .. start+n-1 of stream ``key``."""
+    ctr = torch.arange(start + 1, start + 1 + n, dtype=torch.int64, device=device)
+    z = _mix64_t(ctr * _s64(GOLDEN) + _s64(key))
+    top = _shr(z, 11).to(torch.float64)
+    return (top + 0.5) * (2.0 ** -53)
+
+
+def cnormal(key: int, n: int, var: float = 1.0, device="cpu", start: int = 0) -> torch.Tensor:
+    """n samples of CN(0, var) as complex128 (counters 2i, 2i+1 per sample)."""
+    u = uniform(key, 2 * start, 2 * n, device).view(n, 2)
+    r = torch.sqrt(-2.0 * torch.log(u[:, 0]))
+    th = (2.0 * math.pi) * u[:, 1]
+    s = math.sqrt(var / 2.0)
+    return torch.complex(s * r * torch.cos(th), s * r * torch.sin(th))
+
+
+def taps(seed: int, T: int, instance: int = 0, device="cpu") -> torch.Tensor:
+    """FIR taps h[0..T) ~ CN(0, 1/T), complex64."""
+    return cnormal(stream_key(seed, TAG_TAPS, instance), T, 1.0 / T, device).to(torch.complex64)
+
+
+def hmat(seed: int, N: int, instance: int = 0, device="cpu") -> torch.Tensor:
+    """H ~ CN(0, 1/N) entries, [N, N] row-major complex64."""
+    return cnormal(stream_key(seed, TAG_H, instance), N * N, 1.0 / N, device).to(torch.complex64).view(N, N)
+
+
+def burst_mask(seed: int, F: int, p: float, instance: int, frame: int, device="cpu") -> torch.Tensor:
+    """Bool [F]: exactly round(p * F) burst blocks, chosen without replacement."""
+    nb = int(math.floor(p * F + 0.5))
+    u = uniform(stream_key(seed, TAG_BURST, instance, frame), 0, F, device)
+    order = torch.argsort(u, stable=True)
+    m = torch.zeros(F, dtype=torch.bool, device=device)
+    m[order[:nb]] = True
+    return m
+
+
+def frame(seed: int, F: int, B: int, p: float, instance: int, k: int, device="cpu") -> torch.Tensor:
+    """Frame k of one instance: [F, B] complex64, CN(0, 1) with the burst
+    blocks scaled by 4 in amplitude."""
+    x = cnormal(stream_key(seed, TAG_X, instance, k), F * B, 1.0, device).view(F, B)
+    m = burst_mask(seed, F, p, instance, k, device)
+    x = torch.where(m[:, None], 4.0 * x, x)
+    return x.to(torch.complex64)
+
+
+def frame_uniform(seed: int, tag: int, instance: int, k: int) -> float:
+    """One seeded U(0, 1) draw per (tag, instance, frame)."""
+    return float(uniform(stream_key(seed, tag, instance, k), 0, 1)[0])
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+@dataclass
+class PlainWorkload:
+    """One graph instance: F blocks of B complex samples per frame, T taps,
+    N x N matrix H, DET threshold tau, and a burst fraction per frame that is
+    either fixed (``p``) or drawn U(p_lo, p_hi) per frame."""
+    name: str
+    F: int
+    B: int
+    T: int
+    N: int
+    frames: int
+    tau: float
+    seed: int
+    p: float | None = 0.25
+    p_lo: float = 0.1
+    p_hi: float = 0.9
+    C: int = 3
+
+    def burst_fraction(self, k: int, instance: int = 0) -> float:
+        if self.p is not None:
+            return self.p
+        u = frame_uniform(self.seed, TAG_FRAC, instance, k)
+        return self.p_lo + (self.p_hi - self.p_lo) * u
+
+    def frame(self, k: int, device="cpu", instance: int = 0) -> torch.Tensor:
+        return frame(self.seed, self.F, self.B, self.burst_fraction(k, instance), instance, k, device)
+
+    def frames_tensor(self, k0: int, n: int, device="cpu", instance: int = 0) -> torch.Tensor:
+        return torch.stack([self.frame(k, device, instance) for k in range(k0, k0 + n)])
+
+    def taps(self, device="cpu", instance: int = 0):
+        return taps(self.seed, self.T, instance, device)
+
+    def H(self, device="cpu", instance: int = 0):
+        return hmat(self.seed, self.N, instance, device)
+
+    @property
+    def samples_per_frame(self) -> int:
+        return self.F * self.B
+
+
+# Plain graph, 100 frames of 64 blocks x 256 samples, 25% burst blocks,
+# 16 taps, H 16x16, tau = 4B.
+PLAIN_SMALL = PlainWorkload("plain_F64_B256_T16_N16_100fr", F=64, B=256, T=16, N=16, frames=100,
+                            tau=4.0 * 256, seed=1, p=0.25)
+# Plain graph, 1000 frames of 4096 blocks x 1024 samples, burst fraction
+# U(0.1, 0.9) per frame, 64 taps, H 32x32, tau = 4B.
+PLAIN_LARGE = PlainWorkload("plain_F4096_B1024_T64_N32_1000fr", F=4096, B=1024, T=64, N=32,
+                            frames=1000, tau=4.0 * 1024, seed=2, p=None, p_lo=0.1, p_hi=0.9)
+
+
+@dataclass
+class BatchedWorkload:
+    """Many independent graph instances with uneven shapes: F log-uniform in
+    [F_lo, F_hi], T drawn from ``T_choices``, per-instance burst fraction
+    U(p_lo, p_hi) and tau = kappa * B with kappa ~ U(kappa_lo, kappa_hi)."""
+    name: str
+    instances: int
+    B: int
+    N: int
+    seed: int
+    F_lo: int = 16
+    F_hi: int = 4096
+    T_choices: tuple = (8, 32, 128)
+    p_lo: float = 0.05
+    p_hi: float = 0.95
+    kappa_lo: float = 2.0
+    kappa_hi: float = 8.0
+    frames: int = 1
+    shapes: list = field(default_factory=list)
+
+    def __post_init__(self):
+        self.shapes = []
+        for i in range(self.instances):
+            u = uniform(stream_key(self.seed, TAG_SHAPE, i), 0, 4)
+            F = int(math.floor(math.exp(math.log(self.F_lo) + float(u[0]) * (math.log(self.F_hi) - math.log(self.F_lo)))))
+            F = max(self.F_lo, min(self.F_hi, F))
+            T = self.T_choices[min(int(float(u[1]) * len(self.T_choices)), len(self.T_choices) - 1)]
+            p = self.p_lo + (self.p_hi - self.p_lo) * float(u[2])
+            kappa = self.kappa_lo + (self.kappa_hi - self.kappa_lo) * float(u[3])
+            self.shapes.append({"F": F, "T": T, "p": p, "tau": float(kappa * self.B)})
+
+    def instance(self, i: int) -> PlainWorkload:
+        s = self.shapes[i]
+        return PlainWorkload(f"{self.name}[{i}]", F=s["F"], B=self.B, T=s["T"], N=self.N,
+                             frames=self.frames, tau=s["tau"], seed=self.seed * 100003 + i, p=s["p"])
+
+
+# 512 instances, F log-uniform in [16, 4096], B = 256, T in {8, 32, 128},
+# H 64x64 per instance.
+BATCHED = BatchedWorkload("batched_512x_B256_N64", instances=512, B=256, N=64, seed=3)
