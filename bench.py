@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the PRUNE firing path on B300: graph Msamples/s.
+
+One step fires the whole hot path (FIR with delay line, DET, SEL, HX_b,
+SINK) over the whole synthetic stream of the workload (default: the plain
+graph with 1000 frames of F = 4096 blocks x B = 1024 complex64 samples,
+T = 64 taps, H 32 x 32, tau = 4B, burst fraction U(0.1, 0.9) per frame).
+Inputs are resident in HBM (32 GiB per step, far above the 126 MB L2, so no
+L2 flush is needed) and pushed into f0 by reference; results stay in the
+result ring.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank fires its own graph instance (independent streams,
+instance sharding with no collective: weak scaling); rank 0 prints the line
+with the samples of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_06625_b300 import synth  # noqa: E402
+
+METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 latency"
+UNIT = "Msamples/s"
+# FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
+# FP32 lanes x 2 flop x 2.032 GHz.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+KIND_NAMES = {0: "f0_push_kernel", 1: "fir_energy_kernel", 2: "det_sel_kernel", 3: "hx_cuda_kernel",
+              4: "hx_tc_kernel", 5: "firing_loop_kernel"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def max_over_ranks(v, ws, dev):
+    if ws == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, ws, dev):
+    if ws == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_sample(w, frames, first=0, instance=0):
+    """Time the FP64 oracle on `frames` frames of the workload (the delay
+    token before the first frame comes from the input).  Returns
+    (Msamples/s, seconds, frames)."""
+    import oracle
+    oracle.build()
+    xs = w.frames_tensor(first, frames, instance=instance).numpy()
+    hist = None
+    if first > 0 and w.T > 1:
+        hist = w.frame(first - 1, instance=instance).numpy().reshape(-1)[-(w.T - 1):].astype(np.complex128)
+    taps, H = w.taps(instance=instance).numpy(), w.H(instance=instance).numpy()
+    t0 = time.perf_counter()
+    oracle.run(w.F, w.B, w.T, w.N, np.float32(w.tau), taps, H, xs, C=w.C, hist_in=hist)
+    dt = time.perf_counter() - t0
+    return frames * w.F * w.B / dt / 1e6, dt, frames
+
+
+def run_reference(args, w):
+    """--impl reference: the oracle, as it stands, timed on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = args.ref_frames
+    for _ in range(args.warmup):
+        oracle_sample(w, per_step, first=0)
+    t = 0.0
+    for s in range(args.steps):
+        _, dt, _ = oracle_sample(w, per_step, first=1 + s)
+        t += dt
+    value = args.steps * per_step * w.F * w.B / t / 1e6
+    sample = f"{per_step} frame(s) of {w.name} per step, single-threaded FP64 C oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 + Box-Muller)",
+            "config": {"workload": w.name, "F": w.F, "B": w.B, "T": w.T, "N": w.N, "frames_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def make_inputs(w, frames, dev, instance):
+    x = torch.empty(frames, w.F, w.B, dtype=torch.complex64, device=dev)
+    for k in range(frames):
+        x[k] = w.frame(k, device=dev, instance=instance)
+    return x
+
+
+def run_ours(args, w):
+    from paper_1802_06625_b300 import _lib
+    from paper_1802_06625_b300.graph import Graph
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+
+    frames = args.frames or w.frames
+    C = args.C
+    x = make_inputs(w, frames, dev, instance=rank)
+    stream = torch.cuda.Stream(device=dev)
+    g = Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(instance=rank), w.H(instance=rank), C=C, out_frames=frames,
+              stream=stream, device=local)
+    L = w.F * w.B
+
+    def step():
+        for k in range(0, frames, C):
+            m = min(C, frames - k)
+            g.push(x[k:k + m], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+            g.run(actors=args.actors)
+        g.discard()
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+    g.profile(True)
+    for kind in range(6):
+        g.kernel_times(kind, reset=True)
+
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    times = {k: g.kernel_times(k, reset=True) for k in range(6)}
+    g.profile(False)
+    launches = sum(n for _, n in times.values())
+    samples = sum_over_ranks(float(args.steps * frames * L), ws, dev)
+    value = samples / (ms / 1e3) / 1e6
+
+    # dominant kernel and its roofline (algorithmic work per launch / avg duration)
+    kind, (kms, kn) = max(times.items(), key=lambda kv: kv[1][0])
+    peaks = measured_peaks()
+    runs = args.steps * ((frames + C - 1) // C)
+    roof = None
+    if kn:
+        avg_s = kms / kn / 1e3
+        frames_per_launch = args.steps * frames / kn if kind in (1, 2, 5) else args.steps * frames / kn
+        if kind == 1:      # FIR: T complex MACs = 8T flop per sample (CUDA-core FP32)
+            work = 8.0 * w.T * L * frames_per_launch
+            roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"}
+        else:              # HBM-bound kernels: algorithmic bytes per launch
+            nbytes = 16.0 * L * frames_per_launch
+            roof = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": "measured" if not peaks.get("fallback") else "fallback"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = args.traffic
+        roof["kernel"] = KIND_NAMES[kind]
+        roof["avg_launch_ms"] = kms / kn
+        roof["share"] = kms / max(sum(t for t, _ in times.values()), 1e-12)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded SplitMix64 + Box-Muller, generated on device)",
+            "config": {"workload": w.name, "F": w.F, "B": w.B, "T": w.T, "N": w.N, "tau": w.tau,
+                       "frames_per_step": frames, "C": C, "path": "actors" if args.actors else "firing_loop",
+                       "l2": "inputs larger than L2 (%.1f GiB per step), no flush" % (frames * L * 8 / 2**30),
+                       "parallelism": f"instance-sharded x{ws}" if ws > 1 else "single instance"},
+            "roofline": roof, "gpu_launches": launches,
+            "kernel_ms_per_step": {KIND_NAMES[k]: t / args.steps for k, (t, n) in times.items() if n},
+            "clocks": clk.summary()}
+
+    # end to end through the public API: host frames in, host records out
+    del g
+    line["e2e"] = run_e2e(args, w, dev, stream, rank, ws)
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt, nf = oracle_sample(w, args.cpu_frames, first=0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {nf} frame(s) of {w.name}, single-threaded FP64 C oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(args, w, dev, stream, rank, ws):
+    from paper_1802_06625_b300 import _lib
+    from paper_1802_06625_b300.graph import Graph
+
+    E = args.e2e_frames
+    C = args.C
+    L = w.F * w.B
+    xh = torch.empty(E, w.F, w.B, dtype=torch.complex64).pin_memory()
+    for k in range(E):
+        xh[k] = w.frame(k, device=dev, instance=rank).cpu()
+    yh = torch.empty(E, w.F, w.B, dtype=torch.complex64).pin_memory()
+    ih = torch.empty(E, w.F, dtype=torch.int32).pin_memory()
+    g = Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(instance=rank), w.H(instance=rank), C=C, out_frames=C,
+              stream=stream, device=dev.index)
+    recs = (_lib.prune_frame_out * C)()
+    lib = _lib.lib()
+
+    def step():
+        d2h = 0
+        for k in range(0, E, C):
+            m = min(C, E - k)
+            _lib.check(lib.prune_push_frames(g.h, xh[k].data_ptr(), m, _lib.PRUNE_MEM_HOST), g.h)
+            g.run()
+            for i in range(m):
+                recs[i].idx = ih[k + i].data_ptr()
+                recs[i].y = yh[k + i].data_ptr()
+            n = ctypes.c_int32()
+            _lib.check(lib.prune_pull(g.h, recs, m, ctypes.byref(n), _lib.PRUNE_MEM_HOST), g.h)
+            for i in range(n.value):
+                d2h += recs[i].c * (w.B * 8 + 4) + 12
+        return d2h
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        d2h += step()
+    torch.cuda.synchronize(dev)
+    dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    g.close()
+    samples = sum_over_ranks(float(args.steps * E * L), ws, dev)
+    return {"value": samples / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": E * L * 8,
+            "d2h_bytes_per_step": d2h // args.steps, "frames_per_step": E,
+            "note": "pinned host frames pushed (H2D) and records pulled (D2H) through the C ABI"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
+    ap.add_argument("--frames", type=int, default=0, help="frames per step (default: the workload's)")
+    ap.add_argument("--C", type=int, default=3, help="buffering constant of eq. (2)")
+    ap.add_argument("--actors", action="store_true", help="one kernel per actor instead of the fused loop")
+    ap.add_argument("--e2e-frames", type=int, default=48)
+    ap.add_argument("--cpu-frames", type=int, default=8)
+    ap.add_argument("--ref-frames", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the top kernel")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = synth.PLAIN_LARGE if args.workload == "plain_large" else synth.PLAIN_SMALL
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

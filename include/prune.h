@@ -1,0 +1,252 @@
+/*
+ * prune.h - C ABI of the B300 firing runtime for PRUNE dynamic dataflow
+ * graphs (Boutellier, Wu, Huttunen, Bhattacharyya, "PRUNE: Dynamic and
+ * Decidable Dataflow for Signal Processing on Heterogeneous Platforms").
+ *
+ * The graph this library fires is the canonical dynamic, decidable graph
+ *
+ *   SRC -f0-> FIR -f2-> DET (configuration actor) -f4-> SEL.cport
+ *              |  \                               -f5-> SINK.cport
+ *              f1  -f3-> SEL (dynamic) -f6_b-> HX_b (static) -f7_b-> SINK (dynamic)
+ *
+ * with b = 0..F-1 (Sec. III: actors, ports, FIFOs; Sec. V: one DPG with
+ * configuration actor DET, dynamic actors SEL and SINK and F dynamic
+ * components HX_b).  Per frame:
+ *   FIR  (static actor)    y[n] = sum_{t<T} h[t] x[n-t] over the continuous
+ *                          stream; the last T-1 input samples are the delay
+ *                          token carried on the self-loop FIFO f1 (Sec. III-D;
+ *                          initial token: T-1 zeros).
+ *   DET  (configuration)   E_b = sum_{n<B} |y[bB+n]|^2, v[b] = (E_b > tau);
+ *                          emits one control token (Sec. III-B/C).
+ *   SEL  (dynamic, x)      consumes the F blocks of y and the control token;
+ *                          DRP_b fires at rate BTOI(v[b]) * 1 (eq. (1)).
+ *   HX_b (static, DC b)    X = reshape(block, (B/N, N)) row-major,
+ *                          out[j*N+i] = sum_k H[i][k] X[j][k].
+ *   SINK (dynamic, y)      consumes the control token and c = sum_b v[b]
+ *                          blocks; emits the record (frame, c, idx[c], out[c][B])
+ *                          with idx ascending.
+ *
+ * Conventions for every entry point:
+ *   - complex samples are complex64: two float32 (re, im), interleaved;
+ *   - "device" pointers are CUDA device (or managed) memory of the graph's
+ *     device; "host" pointers are CPU memory (pageable or pinned);
+ *   - nothing is retained after return unless stated (borrowed frames);
+ *   - no C++ exception crosses this interface; every function returns a
+ *     prune_status and, on failure, sets a message read by prune_last_error;
+ *   - a prune_graph is used by one host thread at a time;
+ *   - work is enqueued on the graph's CUDA stream; functions that return data
+ *     to the host (pull, peek, sync, fifo_stats) wait for it.
+ * There is no CPU implementation of any step: without a usable CUDA device
+ * every compute entry point returns PRUNE_ECUDA.
+ */
+#ifndef PRUNE_H
+#define PRUNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PRUNE_API __attribute__((visibility("default")))
+#else
+#define PRUNE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum prune_status {
+  PRUNE_OK = 0,
+  PRUNE_EINVAL = 1,   /* bad argument, shape, or a rate/rule violation of the graph */
+  PRUNE_ENOMEM = 2,   /* allocation failed or the graph would exceed its HBM budget */
+  PRUNE_EAGAIN = 3,   /* FIFO full (push) or empty (pull): nothing was done */
+  PRUNE_ETIMEOUT = 4, /* a bounded device-side wait gave up; the graph is poisoned */
+  PRUNE_ECUDA = 5,    /* a CUDA call failed (no device, launch error, ...) */
+  PRUNE_EBUSY = 6,    /* the request conflicts with work in flight */
+  PRUNE_EDEVICE = 7   /* a device-side invariant check failed; the graph is poisoned */
+} prune_status;
+
+/* FIFO identifiers for prune_fifo_stats (see the graph above).  PRUNE_FIFO_F6
+ * and PRUNE_FIFO_F7 aggregate the F per-DC FIFOs f6_b / f7_b. */
+enum {
+  PRUNE_FIFO_F0 = 0, /* SRC -> FIR           token: one block   rate F */
+  PRUNE_FIFO_F1 = 1, /* FIR -> FIR (delay 1) token: T-1 samples rate 1 */
+  PRUNE_FIFO_F2 = 2, /* FIR -> DET           token: one block   rate F */
+  PRUNE_FIFO_F3 = 3, /* FIR -> SEL           token: one block   rate F */
+  PRUNE_FIFO_F4 = 4, /* DET -> SEL.cport     control token      rate 1 */
+  PRUNE_FIFO_F5 = 5, /* DET -> SINK.cport    control token      rate 1 */
+  PRUNE_FIFO_F6 = 6, /* SEL -> HX_b          one block, atr 1 / itr 0 */
+  PRUNE_FIFO_F7 = 7, /* HX_b -> SINK         one block, atr 1 / itr 0 */
+  PRUNE_NUM_FIFOS = 8
+};
+
+/* Memory kinds for prune_push_frames / prune_pull. */
+enum {
+  PRUNE_MEM_HOST = 0,          /* host pointer: copied host -> device */
+  PRUNE_MEM_DEVICE = 1,        /* device pointer: copied device -> device */
+  PRUNE_MEM_DEVICE_BORROW = 2, /* device pointer, referenced in place (push only) */
+  PRUNE_MEM_DISCARD = 3        /* pull only: drop the records without copying */
+};
+
+/* prune_run flags. */
+enum {
+  PRUNE_RUN_ASYNC = 0,   /* return once the firings are enqueued */
+  PRUNE_RUN_SYNC = 1,    /* return once they completed (device status checked) */
+  PRUNE_RUN_ACTORS = 2   /* fire one kernel per actor instead of the fused firing
+                            loop (same results; FIFOs f2/f3 materialised in HBM) */
+};
+
+typedef struct prune_graph prune_graph;
+
+/* Graph descriptor.  Sizes: F >= 1 blocks per frame (the rate of f0, f2, f3
+ * and the number of DCs); B complex samples per block, a multiple of 8 in
+ * [8, 2048] with B/8 a power of two up to 32 or a multiple of 32; T FIR taps,
+ * 1 <= T <= 256, T - 1 <= B; N divides B, 1 <= N <= 128.
+ * C is the buffering constant of eq. (2) (Sec. VI-B; 0 selects 3): f0 holds C
+ * frames (F*C block tokens), f1 holds max(C, 1) delay tokens.  out_frames is
+ * the capacity of the result ring in frames (0 selects C). */
+typedef struct prune_graph_desc {
+  int32_t F, B, T, N;
+  int32_t C;
+  int32_t out_frames;
+  float tau;            /* DET threshold; v[b] = (E_b > tau) */
+  const float *taps;    /* host, 2*T floats: h[t] = (taps[2t], taps[2t+1]); copied */
+  const float *H;       /* host, 2*N*N floats, row-major H[i][k]; copied */
+  void *stream;         /* cudaStream_t to enqueue on, or NULL for a graph-owned stream */
+  int32_t device;       /* CUDA device ordinal, or -1 for the current device */
+  int32_t reserved;
+  uint64_t hbm_budget;  /* bytes the graph may allocate on the device; 0 = no limit */
+} prune_graph_desc;
+
+/* One frame record produced by SINK. */
+typedef struct prune_frame_out {
+  int64_t frame;  /* out: frame sequence number, 0 for the first frame pushed */
+  int32_t c;      /* out: selected blocks (the DPG firing rate of this frame) */
+  int32_t reserved;
+  int32_t *idx;   /* in: caller buffer of F int32 (host or device per flags) */
+  void *y;        /* in: caller buffer of F*B complex64; receives c*B samples */
+} prune_frame_out;
+
+/* Zero-copy view of a finished record that is still in the result ring. */
+typedef struct prune_frame_view {
+  int64_t frame;
+  int32_t c;
+  int32_t reserved;
+  const int32_t *idx; /* device pointer, c entries */
+  const void *y;      /* device pointer, c*B complex64 */
+} prune_frame_view;
+
+/* Eq. (2), Sec. VI-B: capacity in tokens of a FIFO with rate r, delay Q and
+ * buffering constant C: r*C+Q if Q is not a multiple of r, else max(r*C, Q).
+ * Host only.  EINVAL if r < 1, Q < 0 or C < 1. */
+PRUNE_API prune_status prune_fifo_capacity(int64_t r, int64_t Q, int64_t C, int64_t *cap);
+
+/* Validate the descriptor (shapes above; rates of every port match its FIFO,
+ * Sec. III-A), size the FIFOs by eq. (2), allocate the device state (FIFO
+ * rings, device-side head/tail counters, delay token = T-1 zeros, taps, H) and
+ * upload it.  *out receives the graph, or NULL on error (see
+ * prune_last_error(NULL)).  ENOMEM if the allocation exceeds hbm_budget. */
+PRUNE_API prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out);
+
+/* Free every device and host resource of the graph after waiting for its
+ * work.  Safe on NULL. */
+PRUNE_API prune_status prune_graph_destroy(prune_graph *g);
+
+/* Push n frames ([n][F][B] complex64) into f0 (the SRC actor's firings).
+ * mem = PRUNE_MEM_HOST: x is host memory, copied asynchronously on the
+ *   graph's stream (pinned memory must stay unchanged until the frames were
+ *   fired, e.g. until prune_run(..., PRUNE_RUN_SYNC) or a pull of them);
+ * PRUNE_MEM_DEVICE: x is device memory, copied on the stream;
+ * PRUNE_MEM_DEVICE_BORROW: x is device memory that f0 references in place;
+ *   it must stay valid and unchanged until the frames were fired (work that
+ *   the caller orders on the graph's stream after prune_run is safe).
+ * EAGAIN (and nothing pushed) if f0 lacks n*F free block slots. */
+PRUNE_API prune_status prune_push_frames(prune_graph *g, const void *x, int32_t n, int32_t mem);
+
+/* Fire the whole graph (FIR, DET, SEL, HX_b, SINK) on up to max_frames pushed
+ * frames, in order, as far as the blocking rules allow (f0 tokens present and
+ * room in the result ring).  The control tokens are dispatched on the device:
+ * the host never reads c between DET and SINK.  *n_fired (optional) receives
+ * the number of frames enqueued.  flags: PRUNE_RUN_*.  With PRUNE_RUN_SYNC a
+ * device error (ETIMEOUT, EDEVICE) of these firings is returned here;
+ * otherwise at the next pull, peek, sync or fifo_stats. */
+PRUNE_API prune_status prune_run(prune_graph *g, int32_t max_frames, int32_t *n_fired, int32_t flags);
+
+/* Wait for all work of the graph; report device-side errors. */
+PRUNE_API prune_status prune_sync(prune_graph *g);
+
+/* Pop up to max finished records (oldest first) into outs[0..max).  Waits for
+ * the records that were fired.  mem = PRUNE_MEM_HOST or PRUNE_MEM_DEVICE
+ * for the idx/y buffers, or PRUNE_MEM_DISCARD to drop the records (idx/y
+ * ignored; frame and c still filled if outs is not NULL).  *n receives the
+ * number popped.  EAGAIN if no fired frame is waiting.  A DISCARD with outs ==
+ * NULL does not wait: the dropped slots are reused by later firings in stream
+ * order. */
+PRUNE_API prune_status prune_pull(prune_graph *g, prune_frame_out *outs, int32_t max, int32_t *n, int32_t mem);
+
+/* View the i-th oldest unpulled record in place (device pointers valid until
+ * it is pulled).  Waits for it.  EAGAIN if fewer than i+1 records wait. */
+PRUNE_API prune_status prune_peek(prune_graph *g, int32_t i, prune_frame_view *view);
+
+/* Cumulative token counters of one FIFO, read from the device: tokens
+ * written (excluding initial tokens), tokens read, and the peak occupancy
+ * observed when tokens were committed.  Waits for the graph's work. */
+PRUNE_API prune_status prune_fifo_stats(prune_graph *g, int32_t fifo, uint64_t *written, uint64_t *read,
+                              uint64_t *peak);
+
+/* Capacity in tokens that the graph gave a FIFO (eq. (2)). */
+PRUNE_API prune_status prune_fifo_capacity_of(prune_graph *g, int32_t fifo, int64_t *cap);
+
+/* Per-kernel timing for measurement.  With enable != 0 the graph records a
+ * CUDA event pair around every kernel it launches on its stream; kernel
+ * kinds: 0 = f0 push commit, 1 = FIR(+energy), 2 = DET+SEL, 3 = HX on CUDA
+ * cores, 4 = HX on tensor cores, 5 = fused firing loop.  prune_kernel_times
+ * waits for the graph, returns the summed device milliseconds and launch
+ * count of one kind since the last reset, and resets that kind if reset != 0. */
+PRUNE_API prune_status prune_profile(prune_graph *g, int32_t enable);
+PRUNE_API prune_status prune_kernel_times(prune_graph *g, int32_t kind, double *ms, int64_t *launches,
+                                          int32_t reset);
+
+/* Message of the last failure on g (or of the last failed create when g is
+ * NULL, per host thread).  Never NULL; valid until the next call on g. */
+PRUNE_API const char *prune_last_error(const prune_graph *g);
+
+/* ------------------------------------------------------------------------
+ * Single-actor entry points on caller device buffers (stream-ordered,
+ * asynchronous, no graph object).  They fire one actor (or one fused actor
+ * pair) over `frames` consecutive frames of one instance and exist so that
+ * each actor can be checked and timed on its own.
+ * ---------------------------------------------------------------------- */
+
+/* FIR actor with the DET energy reduction in its epilogue.
+ *   x        device, [frames][F*B] complex64, the frames back to back
+ *   hist     device, T-1 complex64: delay token before frame 0 (NULL = zeros)
+ *   taps     device, T complex64
+ *   y        device, [frames][F*B] complex64 output (may be NULL: energies only)
+ *   energy   device, [frames][F] float32 block energies E_b (may be NULL)
+ *   hist_out device, T-1 complex64: the delay token after the last frame (may be NULL)
+ * Sizes as in prune_graph_desc. */
+PRUNE_API prune_status prune_fir_energy(const void *x, const void *hist, const void *taps, int32_t F,
+                              int32_t B, int32_t T, int32_t frames, void *y, float *energy,
+                              void *hist_out, void *stream);
+
+/* DET + SEL control path: v[b] = (energy[k][b] > tau); c[k] = sum_b v[b];
+ * idx[k][0..c) = ascending b with v[b] (warp ballot and prefix scan).
+ *   energy device [frames][F] float32; c device [frames] int32;
+ *   idx device [frames][F] int32 (entries >= c[k] are left unchanged). */
+PRUNE_API prune_status prune_det_sel(const float *energy, int32_t F, int32_t frames, float tau, int32_t *c,
+                           int32_t *idx, void *stream);
+
+/* HX_b over the compacted blocks (SEL's output DRPs, in place):
+ *   out[k][j] = HX(y[k][idx[k][j]]) for j < c[k], where c and idx are read on
+ *   the device.  y device [frames][F*B]; H device [N][N] complex64;
+ *   out device [frames][F*B] (first c[k]*B samples of each frame written).
+ * N < 64 runs on CUDA cores; N >= 64 on tcgen05 tensor cores (3-pass split
+ * FP16 products, FP32 accumulation). */
+PRUNE_API prune_status prune_hx(const void *y, const int32_t *idx, const int32_t *c, int32_t F, int32_t B,
+                      int32_t N, int32_t frames, const void *H, void *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRUNE_H */

@@ -1,0 +1,99 @@
+"""ctypes binding of libprune.so: the C ABI of include/prune.h, same names.
+
+Argument marshalling only: every step of the dataflow runs in the CUDA
+kernels of the library.  Importing this module loads the library and fails
+loudly if it is missing (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+P = ctypes.c_void_p
+I32, I64, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+
+PRUNE_OK, PRUNE_EINVAL, PRUNE_ENOMEM, PRUNE_EAGAIN = 0, 1, 2, 3
+PRUNE_ETIMEOUT, PRUNE_ECUDA, PRUNE_EBUSY, PRUNE_EDEVICE = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EAGAIN", 4: "ETIMEOUT", 5: "ECUDA",
+                6: "EBUSY", 7: "EDEVICE"}
+PRUNE_MEM_HOST, PRUNE_MEM_DEVICE, PRUNE_MEM_DEVICE_BORROW, PRUNE_MEM_DISCARD = 0, 1, 2, 3
+PRUNE_RUN_ASYNC, PRUNE_RUN_SYNC, PRUNE_RUN_ACTORS = 0, 1, 2
+PRUNE_NUM_FIFOS = 8
+
+EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "prune_push_frames",
+           "prune_run", "prune_sync", "prune_pull", "prune_peek", "prune_fifo_stats",
+           "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx")
+
+
+class prune_graph_desc(ctypes.Structure):
+    _fields_ = [("F", I32), ("B", I32), ("T", I32), ("N", I32), ("C", I32), ("out_frames", I32),
+                ("tau", ctypes.c_float), ("taps", P), ("H", P), ("stream", P), ("device", I32),
+                ("reserved", I32), ("hbm_budget", U64)]
+
+
+class prune_frame_out(ctypes.Structure):
+    _fields_ = [("frame", I64), ("c", I32), ("reserved", I32), ("idx", P), ("y", P)]
+
+
+class prune_frame_view(ctypes.Structure):
+    _fields_ = [("frame", I64), ("c", I32), ("reserved", I32), ("idx", P), ("y", P)]
+
+
+class PruneError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libprune.so not built at {path}: run `python -m paper_1802_06625_b300.build`")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "prune_fifo_capacity": [I64, I64, I64, ctypes.POINTER(I64)],
+        "prune_graph_create": [ctypes.POINTER(prune_graph_desc), ctypes.POINTER(P)],
+        "prune_graph_destroy": [P],
+        "prune_push_frames": [P, P, I32, I32],
+        "prune_run": [P, I32, ctypes.POINTER(I32), I32],
+        "prune_sync": [P],
+        "prune_pull": [P, P, I32, ctypes.POINTER(I32), I32],
+        "prune_peek": [P, I32, ctypes.POINTER(prune_frame_view)],
+        "prune_fifo_stats": [P, I32, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)],
+        "prune_fifo_capacity_of": [P, I32, ctypes.POINTER(I64)],
+        "prune_profile": [P, I32],
+        "prune_kernel_times": [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I32],
+        "prune_fir_energy": [P, P, P, I32, I32, I32, I32, P, P, P, P],
+        "prune_det_sel": [P, I32, I32, ctypes.c_float, P, P, P],
+        "prune_hx": [P, P, P, I32, I32, I32, I32, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.prune_last_error.argtypes = [P]
+    lib.prune_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def check(status: int, g=None):
+    if status != PRUNE_OK:
+        msg = lib().prune_last_error(g).decode(errors="replace")
+        raise PruneError(status, msg)
+    return status

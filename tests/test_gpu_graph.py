@@ -1,0 +1,151 @@
+"""The whole graph through the C ABI against the oracle: plain workloads,
+ragged and degenerate shapes, FIFO counters, and host-side error paths."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import TOL_REL, compare_frame
+from paper_1802_06625_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1802_06625_b300 import graph
+    return graph
+
+
+def run_graph(G, w, x, actors=False, C=None, out_frames=0, mem=None, chunk=None):
+    """Push, fire and pull all frames of x [n, F, B]; returns records, stats."""
+    C = C or w.C
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=C, out_frames=out_frames)
+    n = x.shape[0]
+    recs = []
+    k = 0
+    xd = x if mem is None else x
+    while k < n:
+        m = min(chunk or C, n - k)
+        g.push(xd[k:k + m], mem=mem)
+        assert g.run(actors=actors) == m
+        recs += g.pull()
+        k += m
+    stats = g.fifo_stats()
+    caps = [g.capacity(f) for f in range(8)]
+    g.close()
+    return recs, stats, caps
+
+
+def check_against_oracle(w, x_np, recs, stats=None, caps=None):
+    r = oracle.run(w.F, w.B, w.T, w.N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), x_np, C=w.C)
+    assert len(recs) == len(r.c)
+    worst, bands = 0.0, 0
+    for k, (frame, c, idx, y) in enumerate(recs):
+        assert frame == k
+        err, rms, nb = compare_frame(c, idx, y, r.c[k], r.idx[k], r.y[k], r.energy[k], np.float32(w.tau), w.B)
+        if rms > 0:
+            worst = max(worst, err / rms)
+        bands += nb
+    assert worst <= TOL_REL, worst
+    if stats is not None:
+        for f in range(8):
+            w_, rd, peak = stats[f"f{f}"]
+            ow, ordd = r.stats[f"f{f}"][:2]
+            if bands == 0:
+                assert (w_, rd) == (ow, ordd), (f, (w_, rd), (ow, ordd))
+            assert peak <= caps[f]
+    return r, worst, bands
+
+
+@pytest.mark.parametrize("actors", [False, True])
+def test_plain_small_workload_100_frames(G, actors):
+    w = synth.PLAIN_SMALL
+    x = w.frames_tensor(0, w.frames)
+    recs, stats, caps = run_graph(G, w, x.cuda(), actors=actors)
+    r, worst, bands = check_against_oracle(w, x.numpy(), recs, stats, caps)
+    assert bands == 0
+    assert np.all(r.c == 16)
+
+
+@pytest.mark.parametrize("F,B,T,N,C,frames", [(3, 64, 5, 4, 3, 7), (1, 8, 1, 1, 1, 5), (5, 2048, 256, 32, 2, 3),
+                                              (9, 768, 64, 12, 3, 4), (2, 256, 32, 16, 4, 9),
+                                              (40, 256, 9, 8, 3, 5)])
+def test_ragged_and_degenerate_shapes(G, F, B, T, N, C, frames):
+    w = synth.PlainWorkload("t", F=F, B=B, T=T, N=N, frames=frames, tau=4.0 * B, seed=F + B + T, p=0.4, C=C)
+    x = w.frames_tensor(0, frames)
+    for actors in (False, True):
+        recs, stats, caps = run_graph(G, w, x.cuda(), actors=actors, C=C)
+        check_against_oracle(w, x.numpy(), recs, stats, caps)
+
+
+def test_tau_extremes_all_and_none(G):
+    base = synth.PLAIN_SMALL
+    x = base.frames_tensor(0, 4)
+    for tau, want in ((-1.0, base.F), (float("inf"), 0)):
+        w = synth.PlainWorkload("t", F=base.F, B=base.B, T=base.T, N=base.N, frames=4, tau=tau, seed=base.seed)
+        recs, stats, _ = run_graph(G, w, x.cuda())
+        assert [c for _, c, _, _ in recs] == [want] * 4
+        assert stats["f6"][0] == 4 * want and stats["f5"][1] == 4   # SINK fires even at c = 0
+        check_against_oracle(w, x.numpy(), recs)
+
+
+def test_host_push_borrow_and_pull_kinds(G):
+    w = synth.PLAIN_SMALL
+    x = w.frames_tensor(0, 6)
+    ref, _, _ = run_graph(G, w, x.cuda())
+    host, _, _ = run_graph(G, w, x, mem=None)                          # host tensor -> H2D copy
+    borrow, _, _ = run_graph(G, w, x.cuda(), mem=2)                    # borrowed in place
+    for a, b in ((ref, host), (ref, borrow)):
+        for (fa, ca, ia, ya), (fb, cb, ib, yb) in zip(a, b):
+            assert fa == fb and ca == cb and np.array_equal(ia, ib) and np.array_equal(ya, yb)
+
+
+def test_deterministic_runs(G):
+    w = synth.PLAIN_SMALL
+    x = w.frames_tensor(0, 5).cuda()
+    a, _, _ = run_graph(G, w, x)
+    b, _, _ = run_graph(G, w, x)
+    for ra, rb in zip(a, b):
+        assert ra[1] == rb[1] and np.array_equal(ra[2], rb[2]) and np.array_equal(ra[3], rb[3])
+
+
+def test_history_carries_across_runs_and_chunking(G):
+    w = synth.PlainWorkload("t", F=6, B=128, T=48, N=8, frames=10, tau=512.0, seed=11, p=0.5, C=4)
+    x = w.frames_tensor(0, 10)
+    one, _, _ = run_graph(G, w, x.cuda(), chunk=4)
+    two, _, _ = run_graph(G, w, x.cuda(), chunk=1)
+    for ra, rb in zip(one, two):
+        assert ra[1] == rb[1] and np.array_equal(ra[2], rb[2])
+        assert np.max(np.abs(ra[3] - rb[3])) <= 1e-6 * max(1.0, np.max(np.abs(ra[3])))
+    check_against_oracle(w, x.numpy(), one)
+
+
+def test_blocking_rules_on_the_host(G):
+    from paper_1802_06625_b300 import _lib
+    w = synth.PLAIN_SMALL
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=2, out_frames=3)
+    x = w.frames_tensor(0, 4).cuda()
+    assert g.pull() == []                                   # nothing fired: EAGAIN -> empty
+    g.push(x[:2])
+    with pytest.raises(_lib.PruneError) as ei:
+        g.push(x[2:3])                                      # f0 holds C = 2 frames
+    assert ei.value.status == _lib.PRUNE_EAGAIN
+    assert g.run() == 2
+    g.push(x[2:4])
+    assert g.run() == 1                                     # result ring holds 3 frames
+    assert len(g.pull()) == 3
+    assert g.run() == 1
+    assert len(g.pull()) == 1
+    assert g.run() == 0
+    g.close()
+
+
+def test_budget_is_enforced(G):
+    from paper_1802_06625_b300 import _lib
+    w = synth.PLAIN_SMALL
+    with pytest.raises(_lib.PruneError) as ei:
+        G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), hbm_budget=1 << 16)
+    assert ei.value.status == _lib.PRUNE_ENOMEM
