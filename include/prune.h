@@ -92,8 +92,14 @@ enum {
 enum {
   PRUNE_RUN_ASYNC = 0,   /* return once the firings are enqueued */
   PRUNE_RUN_SYNC = 1,    /* return once they completed (device status checked) */
-  PRUNE_RUN_ACTORS = 2   /* fire one kernel per actor instead of the fused firing
+  PRUNE_RUN_ACTORS = 2,  /* fire one kernel per actor instead of the fused firing
                             loop (same results; FIFOs f2/f3 materialised in HBM) */
+  PRUNE_RUN_DEVICE_RULE = 4 /* let the device alone enforce FIR's firing rule on f0:
+                            the host does not bound the run by the frames pushed,
+                            so frames may be pushed later from another stream; a
+                            frame that never arrives makes the bounded device wait
+                            give up (PRUNE_ETIMEOUT after PRUNE_TIMEOUT_MS, default
+                            2000 ms).  Fused firing loop only (N < 64). */
 };
 
 typedef struct prune_graph prune_graph;

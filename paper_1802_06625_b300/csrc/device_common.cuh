@@ -14,7 +14,8 @@ enum DevCode : uint32_t {
   kDevTimeout = 1,     // a bounded wait gave up
   kDevUnderflow = 2,   // an actor found fewer tokens than its firing rule needs
   kDevOverflow = 3,    // a commit would exceed the FIFO capacity (eq. (2))
-  kDevAbort = 4        // another CTA failed first
+  kDevAbort = 4,       // another CTA failed first
+  kDevInvariant = 5    // a compacted position fell outside the frame
 };
 enum DevActor : uint32_t { kActSrc = 0, kActFir = 1, kActDet = 2, kActSel = 3, kActHx = 4, kActSink = 5 };
 

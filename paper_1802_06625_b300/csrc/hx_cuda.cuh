@@ -40,6 +40,7 @@ __device__ __forceinline__ void hx_bookkeeping(const HxParams &p, int k, int ck)
   fifo_release(p.ctr, 7, ck, 0, p.status, kActSink, frame);              // SINK DRPs
 }
 
+// Shared memory: max(B, N*N) complex (H is staged through it first).
 template <int NT>
 __global__ void __launch_bounds__(kHxThreads) hx_cuda_kernel(HxParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,9 +49,11 @@ __global__ void __launch_bounds__(kHxThreads) hx_cuda_kernel(HxParams p) {
   const int i = tid % NT, g = tid / NT;
   constexpr int RG = kHxThreads / NT;
   const int R = p.B / NT;
+  for (int q = tid; q < NT * NT; q += kHxThreads) xs[q] = p.H[q];
+  __syncthreads();
   float2 h[NT];
 #pragma unroll
-  for (int kk = 0; kk < NT; ++kk) h[kk] = p.H[i * NT + kk];
+  for (int kk = 0; kk < NT; ++kk) h[kk] = xs[i * NT + kk];
   const int64_t total = static_cast<int64_t>(p.frames) * p.F;
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int k = static_cast<int>(w / p.F), j = static_cast<int>(w % p.F);
@@ -63,30 +66,44 @@ __global__ void __launch_bounds__(kHxThreads) hx_cuda_kernel(HxParams p) {
     const float4 *src = reinterpret_cast<const float4 *>(p.y + p.yslot.slot(k) * p.y_stride +
                                                          static_cast<int64_t>(b) * p.B);
     float2 *dst = p.out + p.oslot.slot(k) * p.out_stride + static_cast<int64_t>(j) * p.B;
+    __syncthreads();  // H staging / previous block done
+    float4 *xs4 = reinterpret_cast<float4 *>(xs);
+    for (int q2 = tid; 2 * q2 < p.B; q2 += kHxThreads) xs4[q2] = __ldg(src + q2);
     __syncthreads();
-    for (int q2 = tid; 2 * q2 < p.B; q2 += kHxThreads) {
-      const float4 v = __ldg(src + q2);
-      xs[2 * q2] = make_float2(v.x, v.y);
-      xs[2 * q2 + 1] = make_float2(v.z, v.w);
+    if (NT == 1) {
+      for (int r = g; r < R; r += RG) {
+        float2 a = make_float2(0.f, 0.f);
+        cmac(a, h[0], xs[r]);
+        dst[r] = a;
+      }
+      continue;
     }
-    __syncthreads();
+    // X[r][kk..kk+1] as one aligned float4 broadcast; two rows per pass
     int r = g;
-    for (; r + RG < R; r += 2 * RG) {  // two rows per pass for ILP
+    for (; r + RG < R; r += 2 * RG) {
       float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-      const float2 *x0 = xs + r * NT, *x1 = xs + (r + RG) * NT;
+      const float4 *x0 = reinterpret_cast<const float4 *>(xs + r * NT);
+      const float4 *x1 = reinterpret_cast<const float4 *>(xs + (r + RG) * NT);
 #pragma unroll
-      for (int kk = 0; kk < NT; ++kk) {
-        cmac(a0, h[kk], x0[kk]);
-        cmac(a1, h[kk], x1[kk]);
+      for (int kk = 0; kk < NT; kk += 2) {
+        const float4 u0 = x0[kk / 2], u1 = x1[kk / 2];
+        cmac(a0, h[kk], make_float2(u0.x, u0.y));
+        cmac(a1, h[kk], make_float2(u1.x, u1.y));
+        cmac(a0, h[kk + 1], make_float2(u0.z, u0.w));
+        cmac(a1, h[kk + 1], make_float2(u1.z, u1.w));
       }
       dst[r * NT + i] = a0;
       dst[(r + RG) * NT + i] = a1;
     }
     for (; r < R; r += RG) {
       float2 a0 = make_float2(0.f, 0.f);
-      const float2 *x0 = xs + r * NT;
+      const float4 *x0 = reinterpret_cast<const float4 *>(xs + r * NT);
 #pragma unroll
-      for (int kk = 0; kk < NT; ++kk) cmac(a0, h[kk], x0[kk]);
+      for (int kk = 0; kk < NT; kk += 2) {
+        const float4 u0 = x0[kk / 2];
+        cmac(a0, h[kk], make_float2(u0.x, u0.y));
+        cmac(a0, h[kk + 1], make_float2(u0.z, u0.w));
+      }
       dst[r * NT + i] = a0;
     }
   }

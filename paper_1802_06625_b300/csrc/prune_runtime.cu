@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -90,6 +91,11 @@ struct prune_graph {
   uint64_t *ctr = nullptr;            // [8][3]
   uint32_t *status = nullptr;         // [4]
   LoopScratch *loop = nullptr;        // fused firing-loop scratch
+  uint64_t *look = nullptr;           // [C][tiles] look-back words
+  uint32_t *done = nullptr;           // [C] finished tiles per frame slot
+  uint64_t *ready = nullptr;          // [C] record-final flags (frame seq + 1)
+  unsigned long long ticket_base = 0;
+  uint64_t timeout_ns = 2000000000ull;
   uint16_t *hx_b_ops = nullptr;       // tcgen05 B operands (N >= 64)
   int64_t cap[PRUNE_NUM_FIFOS] = {};
   // optional per-kernel event timing
@@ -140,10 +146,11 @@ prune_status check_device_status(prune_graph *g) {
   CU(g, cudaMemcpy(st, g->status, sizeof st, cudaMemcpyDeviceToHost));
   if (st[0] == kDevOk) return PRUNE_OK;
   static const char *actors[] = {"SRC", "FIR", "DET", "SEL", "HX", "SINK"};
-  static const char *codes[] = {"ok", "bounded wait gave up", "FIFO underflow", "FIFO overflow", "aborted"};
+  static const char *codes[] = {"ok", "bounded wait gave up", "FIFO underflow", "FIFO overflow", "aborted",
+                                "compacted position out of range"};
   char buf[256];
   std::snprintf(buf, sizeof buf, "device: %s in actor %s on FIFO f%u at frame %u",
-                codes[std::min<uint32_t>(st[0], 4)], actors[std::min<uint32_t>(st[1], 5)], st[2], st[3]);
+                codes[std::min<uint32_t>(st[0], 5)], actors[std::min<uint32_t>(st[1], 5)], st[2], st[3]);
   g->poisoned = true;
   g->poison_code = st[0] == kDevTimeout ? PRUNE_ETIMEOUT : PRUNE_EDEVICE;
   return fail(g, g->poison_code, buf);
@@ -212,7 +219,7 @@ int hx_grid(int sms, int64_t work) {
 
 // Launch the CUDA-core HX kernel for N < 64 (register-blocked for powers of two).
 cudaError_t launch_hx_cuda(const HxParams &p, int grid, cudaStream_t s) {
-  const size_t smem_blk = static_cast<size_t>(p.B) * sizeof(float2);
+  const size_t smem_blk = static_cast<size_t>(std::max(p.B, p.N * p.N)) * sizeof(float2);
   switch (p.N) {
     case 1: hx_cuda_kernel<1><<<grid, kHxThreads, smem_blk, s>>>(p); break;
     case 2: hx_cuda_kernel<2><<<grid, kHxThreads, smem_blk, s>>>(p); break;
@@ -234,6 +241,118 @@ cudaError_t launch_hx_cuda(const HxParams &p, int grid, cudaStream_t s) {
 }
 
 }  // namespace
+
+static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n);
+
+static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
+  const prune_graph_desc &d = g->d;
+  const int64_t T1 = std::max(d.T - 1, 1);
+  FirParams fp{};
+  fp.src = FrameSrc{g->f0_ring, nullptr, 0, seq0, g->C};
+  fp.L = g->L;
+  fp.F = d.F; fp.B = d.B; fp.T = d.T; fp.TP = g->TP; fp.TS = g->TS; fp.tiles = g->tiles; fp.frames = n;
+  fp.taps = g->taps;
+  fp.hist = d.T > 1 ? g->hist + (g->runs & 1) * T1 : nullptr;
+  fp.hist_out = d.T > 1 ? g->hist + ((g->runs + 1) & 1) * T1 : nullptr;
+  fp.y = g->y_ring; fp.y_stride = g->L; fp.yslot = SlotMap{seq0, g->C};
+  fp.energy = g->energy; fp.eslot = SlotMap{seq0, g->C};
+  fp.ctr = g->ctr; fp.status = g->status;
+  fp.cap_f1 = g->cap[1]; fp.cap_f2 = g->cap[2]; fp.cap_f3 = g->cap[3];
+  {
+    KTimer kt(g, 1);
+    fir_energy_kernel<<<dim3(g->tiles, n), kFirThreads, fir_smem_bytes(d.T), g->stream>>>(fp);
+  }
+  CU(g, cudaGetLastError());
+
+  DetSelParams dp{};
+  dp.energy = g->energy; dp.eslot = SlotMap{seq0, g->C};
+  dp.F = d.F; dp.frames = n; dp.tau = d.tau;
+  dp.c = g->rec_c; dp.idx = g->rec_idx; dp.rec_frame = g->rec_frame; dp.rslot = SlotMap{seq0, g->out_cap};
+  dp.ctr = g->ctr; dp.status = g->status;
+  dp.cap_f4 = g->cap[4]; dp.cap_f5 = g->cap[5]; dp.cap_f6 = g->cap[6];
+  {
+    KTimer kt(g, 2);
+    det_sel_kernel<<<n, kDetThreads, 0, g->stream>>>(dp);
+  }
+  CU(g, cudaGetLastError());
+
+  HxParams hp{};
+  hp.y = g->y_ring; hp.y_stride = g->L; hp.yslot = SlotMap{seq0, g->C};
+  hp.c = g->rec_c; hp.idx = g->rec_idx; hp.rslot = SlotMap{seq0, g->out_cap};
+  hp.out = g->rec_y; hp.out_stride = g->L; hp.oslot = SlotMap{seq0, g->out_cap};
+  hp.H = g->H; hp.F = d.F; hp.B = d.B; hp.N = d.N; hp.frames = n;
+  hp.ctr = g->ctr; hp.status = g->status; hp.cap_f7 = g->cap[7];
+  if (g->hx_b_ops) {
+    KTimer kt(g, 4);
+    CU(g, launch_hx_tc(hp, g->hx_b_ops, g->sms, g->stream));
+  } else {
+    KTimer kt(g, 3);
+    CU(g, launch_hx_cuda(hp, hx_grid(g->sms, static_cast<int64_t>(n) * d.F), g->stream));
+  }
+  return PRUNE_OK;
+}
+
+template <int NT>
+static cudaError_t launch_loop_nt(const LoopParams &lp, int sms, size_t smem, cudaStream_t s, int *grid_out,
+                                  unsigned long long total) {
+  static int occ_cache[2] = {0, 0};  // per smem class is overkill: recompute when smem changes
+  static size_t occ_smem = 0;
+  (void)occ_cache;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(firing_loop_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, firing_loop_kernel<NT>, kFirThreads, smem);
+  if (e != cudaSuccess) return e;
+  (void)occ_smem;
+  occ = std::max(occ, 1);
+  const int grid = static_cast<int>(std::min<unsigned long long>(total, static_cast<unsigned long long>(sms) * occ));
+  firing_loop_kernel<NT><<<grid, kFirThreads, smem, s>>>(lp);
+  *grid_out = grid;
+  return cudaGetLastError();
+}
+
+static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n) {
+  const prune_graph_desc &d = g->d;
+  const int64_t T1 = std::max(d.T - 1, 1);
+  LoopParams lp{};
+  FirParams &fp = lp.f;
+  fp.src = FrameSrc{g->f0_ring, nullptr, 0, seq0, g->C};
+  fp.L = g->L;
+  fp.F = d.F; fp.B = d.B; fp.T = d.T; fp.TP = g->TP; fp.TS = g->TS; fp.tiles = g->tiles; fp.frames = n;
+  fp.taps = g->taps;
+  fp.hist = d.T > 1 ? g->hist + (g->runs & 1) * T1 : nullptr;
+  fp.hist_out = d.T > 1 ? g->hist + ((g->runs + 1) & 1) * T1 : nullptr;
+  fp.y = nullptr; fp.y_stride = g->L; fp.yslot = SlotMap{seq0, g->C};
+  fp.energy = g->energy; fp.eslot = SlotMap{seq0, g->C};
+  lp.tau = d.tau;
+  lp.look = g->look; lp.done = g->done; lp.ready = g->ready; lp.C = g->C;
+  lp.rec_c = g->rec_c; lp.rec_idx = g->rec_idx; lp.rec_frame = g->rec_frame; lp.rec_y = g->rec_y;
+  lp.rslot = SlotMap{seq0, g->out_cap};
+  lp.H = g->H; lp.N = d.N;
+  lp.ls = g->loop; lp.ticket_base = g->ticket_base; lp.timeout_ns = g->timeout_ns;
+  lp.ctr = g->ctr; lp.status = g->status;
+  for (int i = 0; i < 8; ++i) lp.cap[i] = static_cast<uint64_t>(g->cap[i]);
+  const unsigned long long total = static_cast<unsigned long long>(n) * g->tiles;
+  int grid = 0;
+  cudaError_t e;
+  {
+    KTimer kt(g, 5);
+    switch (d.N) {
+      case 2: e = launch_loop_nt<2>(lp, g->sms, loop_smem_bytes(d.T, 2), g->stream, &grid, total); break;
+      case 4: e = launch_loop_nt<4>(lp, g->sms, loop_smem_bytes(d.T, 4), g->stream, &grid, total); break;
+      case 8: e = launch_loop_nt<8>(lp, g->sms, loop_smem_bytes(d.T, 8), g->stream, &grid, total); break;
+      case 16: e = launch_loop_nt<16>(lp, g->sms, loop_smem_bytes(d.T, 16), g->stream, &grid, total); break;
+      case 32: e = launch_loop_nt<32>(lp, g->sms, loop_smem_bytes(d.T, 32), g->stream, &grid, total); break;
+      default: e = launch_loop_nt<0>(lp, g->sms, loop_smem_bytes(d.T, d.N), g->stream, &grid, total);
+    }
+  }
+  if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("firing loop launch: ") + cudaGetErrorString(e));
+  g->ticket_base += total + static_cast<unsigned long long>(grid);
+  return PRUNE_OK;
+}
 
 // ===================================================================== ABI
 
@@ -341,8 +460,13 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
       (s = galloc(g, &g->rec_idx, static_cast<size_t>(out_cap) * F)) ||
       (s = galloc(g, &g->rec_y, static_cast<size_t>(out_cap) * L)) ||
       (s = galloc(g, &g->ctr, kNumFifos * 3)) || (s = galloc(g, &g->status, 4)) ||
-      (s = galloc(g, &g->loop, 1)))
+      (s = galloc(g, &g->loop, 1)) || (s = galloc(g, &g->look, static_cast<size_t>(C) * g->tiles)) ||
+      (s = galloc(g, &g->done, static_cast<size_t>(C))) || (s = galloc(g, &g->ready, static_cast<size_t>(C))))
     return bail(s);
+  if (const char *tm = std::getenv("PRUNE_TIMEOUT_MS")) {
+    const long long ms = std::atoll(tm);
+    if (ms > 0) g->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
+  }
   if (N >= 64 && hx_tc_supported(N)) {
     if ((s = galloc(g, &g->hx_b_ops, hx_tc_b_elems(N)))) return bail(s);
   }
@@ -355,6 +479,10 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
             cudaMemsetAsync(g->ctr, 0, sizeof(uint64_t) * kNumFifos * 3, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->status, 0, sizeof(uint32_t) * 4, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->loop, 0, sizeof(LoopScratch), g->stream) == cudaSuccess &&
+            cudaMemsetAsync(g->f0_ring, 0, sizeof(void *) * C, g->stream) == cudaSuccess &&
+            cudaMemsetAsync(g->look, 0, sizeof(uint64_t) * C * g->tiles, g->stream) == cudaSuccess &&
+            cudaMemsetAsync(g->done, 0, sizeof(uint32_t) * C, g->stream) == cudaSuccess &&
+            cudaMemsetAsync(g->ready, 0, sizeof(uint64_t) * C, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->rec_c, 0, sizeof(int32_t) * out_cap, g->stream) == cudaSuccess;
   if (ok && g->hx_b_ops) ok = hx_tc_prepare_b(g->H, N, g->hx_b_ops, g->stream) == cudaSuccess;
   // the initial delay token of f1 is present from the start (Q = 1)
@@ -408,67 +536,16 @@ prune_status prune_push_frames(prune_graph *g, const void *x, int32_t n, int32_t
   return PRUNE_OK;
 }
 
-static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n);
-
-static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
-  const prune_graph_desc &d = g->d;
-  const int64_t T1 = std::max(d.T - 1, 1);
-  FirParams fp{};
-  fp.src = FrameSrc{g->f0_ring, nullptr, 0, seq0, g->C};
-  fp.L = g->L;
-  fp.F = d.F; fp.B = d.B; fp.T = d.T; fp.TP = g->TP; fp.TS = g->TS; fp.tiles = g->tiles; fp.frames = n;
-  fp.taps = g->taps;
-  fp.hist = d.T > 1 ? g->hist + (g->runs & 1) * T1 : nullptr;
-  fp.hist_out = d.T > 1 ? g->hist + ((g->runs + 1) & 1) * T1 : nullptr;
-  fp.y = g->y_ring; fp.y_stride = g->L; fp.yslot = SlotMap{seq0, g->C};
-  fp.energy = g->energy; fp.eslot = SlotMap{seq0, g->C};
-  fp.ctr = g->ctr; fp.status = g->status;
-  fp.cap_f1 = g->cap[1]; fp.cap_f2 = g->cap[2]; fp.cap_f3 = g->cap[3];
-  {
-    KTimer kt(g, 1);
-    fir_energy_kernel<<<dim3(g->tiles, n), kFirThreads, fir_smem_bytes(d.T), g->stream>>>(fp);
-  }
-  CU(g, cudaGetLastError());
-
-  DetSelParams dp{};
-  dp.energy = g->energy; dp.eslot = SlotMap{seq0, g->C};
-  dp.F = d.F; dp.frames = n; dp.tau = d.tau;
-  dp.c = g->rec_c; dp.idx = g->rec_idx; dp.rec_frame = g->rec_frame; dp.rslot = SlotMap{seq0, g->out_cap};
-  dp.ctr = g->ctr; dp.status = g->status;
-  dp.cap_f4 = g->cap[4]; dp.cap_f5 = g->cap[5]; dp.cap_f6 = g->cap[6];
-  {
-    KTimer kt(g, 2);
-    det_sel_kernel<<<n, kDetThreads, 0, g->stream>>>(dp);
-  }
-  CU(g, cudaGetLastError());
-
-  HxParams hp{};
-  hp.y = g->y_ring; hp.y_stride = g->L; hp.yslot = SlotMap{seq0, g->C};
-  hp.c = g->rec_c; hp.idx = g->rec_idx; hp.rslot = SlotMap{seq0, g->out_cap};
-  hp.out = g->rec_y; hp.out_stride = g->L; hp.oslot = SlotMap{seq0, g->out_cap};
-  hp.H = g->H; hp.F = d.F; hp.B = d.B; hp.N = d.N; hp.frames = n;
-  hp.ctr = g->ctr; hp.status = g->status; hp.cap_f7 = g->cap[7];
-  if (g->hx_b_ops) {
-    KTimer kt(g, 4);
-    CU(g, launch_hx_tc(hp, g->hx_b_ops, g->sms, g->stream));
-  } else {
-    KTimer kt(g, 3);
-    CU(g, launch_hx_cuda(hp, hx_grid(g->sms, static_cast<int64_t>(n) * d.F), g->stream));
-  }
-  return PRUNE_OK;
-}
-
-static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n) {
-  return run_actor_kernels(g, seq0, n);
-}
-
 prune_status prune_run(prune_graph *g, int32_t max_frames, int32_t *n_fired, int32_t flags) {
   if (n_fired) *n_fired = 0;
   if (!g) return fail(nullptr, PRUNE_EINVAL, "prune_run: NULL graph");
   if (g->poisoned) return fail(g, g->poison_code, "graph is poisoned by an earlier device error: " + g->err);
   if (max_frames < 0) return fail(g, PRUNE_EINVAL, "prune_run: max_frames < 0");
   // Blocking rules on the host view: frames present in f0, room in the result ring.
-  const int64_t ready = g->pushed - g->fired;
+  const bool device_rule = (flags & PRUNE_RUN_DEVICE_RULE) != 0;
+  if (device_rule && ((flags & PRUNE_RUN_ACTORS) || !loop_supported(g->d.N)))
+    return fail(g, PRUNE_EINVAL, "PRUNE_RUN_DEVICE_RULE needs the fused firing loop");
+  const int64_t ready = device_rule ? g->C - (g->fired - std::min(g->pushed, g->fired)) : g->pushed - g->fired;
   const int64_t room = g->out_cap - (g->fired - g->pulled);
   const int32_t n = static_cast<int32_t>(std::min<int64_t>({static_cast<int64_t>(max_frames), ready, room}));
   DeviceGuard dg(g->dev);

@@ -149,3 +149,46 @@ def test_budget_is_enforced(G):
     with pytest.raises(_lib.PruneError) as ei:
         G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), hbm_budget=1 << 16)
     assert ei.value.status == _lib.PRUNE_ENOMEM
+
+
+def test_device_firing_rule_wait_gives_up_cleanly(G, monkeypatch):
+    """The fused loop waits on f0's device counter for a frame that is never
+    pushed; the bounded wait gives up, the status reaches the host as
+    ETIMEOUT, the graph is poisoned and the CUDA context stays usable."""
+    import ctypes
+    from paper_1802_06625_b300 import _lib
+    monkeypatch.setenv("PRUNE_TIMEOUT_MS", "200")
+    w = synth.PLAIN_SMALL
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=3)
+    n = ctypes.c_int32()
+    st = _lib.lib().prune_run(g.h, 1, ctypes.byref(n), _lib.PRUNE_RUN_DEVICE_RULE | _lib.PRUNE_RUN_SYNC)
+    assert n.value == 1
+    assert st == _lib.PRUNE_ETIMEOUT, _lib.lib().prune_last_error(g.h)
+    assert b"bounded wait" in _lib.lib().prune_last_error(g.h)
+    with pytest.raises(_lib.PruneError) as ei:
+        g.push(w.frames_tensor(0, 1).cuda())
+    assert ei.value.status == _lib.PRUNE_ETIMEOUT
+    g.close()
+    # the context still works
+    a = torch.ones(1024, device="cuda")
+    assert float((a * 2).sum()) == 2048.0
+    # a fresh graph fires normally
+    x = w.frames_tensor(0, 3)
+    recs, stats, caps = run_graph(G, w, x.cuda())
+    check_against_oracle(w, x.numpy(), recs, stats, caps)
+
+
+def test_device_firing_rule_with_frames_present(G):
+    """With the frames already pushed, the device-side rule passes at once."""
+    import ctypes
+    from paper_1802_06625_b300 import _lib
+    w = synth.PLAIN_SMALL
+    x = w.frames_tensor(0, 3)
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=3)
+    g.push(x.cuda())
+    n = ctypes.c_int32()
+    _lib.check(_lib.lib().prune_run(g.h, 3, ctypes.byref(n), _lib.PRUNE_RUN_DEVICE_RULE | _lib.PRUNE_RUN_SYNC), g.h)
+    assert n.value == 3
+    recs = g.pull()
+    g.close()
+    check_against_oracle(w, x.numpy(), recs)
