@@ -78,30 +78,60 @@ __device__ __forceinline__ bool bounded_wait(const LoopParams &p, Pred pred, uin
   }
 }
 
-// Decoupled look-back (single thread): publish the tile's count, accumulate
-// the predecessors' aggregates until an inclusive prefix is found, publish
-// the inclusive prefix.  Returns the exclusive prefix, or -1 on failure.
-__device__ __forceinline__ int64_t lookback(const LoopParams &p, uint64_t *words, int tile, uint64_t epoch,
-                                            uint32_t cnt, uint64_t frame) {
+// Decoupled look-back, one warp: publish the tile's count as an aggregate,
+// then read 32 predecessors per round trip, summing aggregates back to the
+// nearest inclusive prefix; publish the inclusive prefix.  Waits (only when
+// a predecessor has not published anything yet) are bounded.  Returns the
+// exclusive prefix on every lane, or -1 on timeout / abort.
+__device__ __forceinline__ int64_t lookback_warp(const LoopParams &p, uint64_t *words, int tile, uint64_t epoch,
+                                                 uint32_t cnt, uint64_t frame, int lane) {
   if (tile == 0) {
-    st_release_u64(&words[0], look_pack(epoch, kLookPrefix, cnt));
+    if (lane == 0) st_release_u64(&words[0], look_pack(epoch, kLookPrefix, cnt));
     return 0;
   }
-  st_release_u64(&words[tile], look_pack(epoch, kLookAgg, cnt));
+  if (lane == 0) st_release_u64(&words[tile], look_pack(epoch, kLookAgg, cnt));
   uint64_t prefix = 0;
-  for (int i = tile - 1; i >= 0; --i) {
-    uint64_t w = 0;
-    const bool ok = bounded_wait(
-        p, [&] {
-          w = ld_acquire_u64(&words[i]);
-          return (w >> 34) == epoch && ((w >> 32) & 3u) != 0;
-        },
-        kActSel, 3, frame);
-    if (!ok) return -1;
-    prefix += static_cast<uint32_t>(w);
-    if (((w >> 32) & 3u) == kLookPrefix) break;
+  int i0 = tile - 1;
+  uint64_t t0 = 0;
+  uint32_t polls = 0;
+  for (;;) {
+    const int i = i0 - lane;
+    uint32_t flag = kLookPrefix, val = 0;  // i < 0: tile 0 always publishes a prefix first
+    if (i >= 0) {
+      const uint64_t w = ld_acquire_u64(&words[i]);
+      flag = (w >> 34) == epoch ? static_cast<uint32_t>((w >> 32) & 3u) : 0u;
+      val = static_cast<uint32_t>(w);
+    }
+    const unsigned incl = __ballot_sync(0xffffffffu, flag == kLookPrefix);
+    const unsigned none = __ballot_sync(0xffffffffu, flag == 0u);
+    const int first = incl ? __ffs(incl) - 1 : 31;          // nearest inclusive prefix
+    const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (none & need) {  // some predecessor up to there has published nothing yet
+      if (polls == 0) t0 = globaltimer_ns();
+      ++polls;
+      __nanosleep(32);
+      if ((polls & 63u) == 0u) {
+        int stop = 0;
+        if (lane == 0) {
+          if (ld_volatile_u32(&p.ls->abort)) stop = 1;
+          else if (globaltimer_ns() - t0 > p.timeout_ns) {
+            report_error(p.status, kDevTimeout, kActSel, 3, frame);
+            atomicExch(&p.ls->abort, 1u);
+            stop = 1;
+          }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return -1;
+      }
+      continue;
+    }
+    uint32_t v = (static_cast<unsigned>(lane) <= static_cast<unsigned>(first)) ? val : 0u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    prefix += v;
+    if (incl) break;
+    i0 -= 32;
   }
-  st_release_u64(&words[tile], look_pack(epoch, kLookPrefix, static_cast<uint32_t>(prefix + cnt)));
+  if (lane == 0) st_release_u64(&words[tile], look_pack(epoch, kLookPrefix, static_cast<uint32_t>(prefix + cnt)));
   return static_cast<int64_t>(prefix);
 }
 
@@ -248,7 +278,10 @@ __global__ void __launch_bounds__(kFirThreads) firing_loop_kernel(LoopParams p) 
     // 4b. SEL across tiles: decoupled look-back for the tile's offset
     const int cnt = s_cnt;
     const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
-    if (tid == 0) s_prefix = lookback(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq);
+    if (warp == 0) {
+      const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
+      if (lane == 0) s_prefix = pr;
+    }
     __syncthreads();
     const long long prefix = s_prefix;
     if (prefix < 0) break;

@@ -72,7 +72,8 @@ def test_plain_small_workload_100_frames(G, actors):
 
 @pytest.mark.parametrize("F,B,T,N,C,frames", [(3, 64, 5, 4, 3, 7), (1, 8, 1, 1, 1, 5), (5, 2048, 256, 32, 2, 3),
                                               (9, 768, 64, 12, 3, 4), (2, 256, 32, 16, 4, 9),
-                                              (40, 256, 9, 8, 3, 5)])
+                                              (40, 256, 9, 8, 3, 5), (37, 256, 128, 64, 3, 3),
+                                              (5, 512, 32, 64, 2, 4)])
 def test_ragged_and_degenerate_shapes(G, F, B, T, N, C, frames):
     w = synth.PlainWorkload("t", F=F, B=B, T=T, N=N, frames=frames, tau=4.0 * B, seed=F + B + T, p=0.4, C=C)
     x = w.frames_tensor(0, frames)
