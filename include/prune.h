@@ -252,6 +252,47 @@ PRUNE_API prune_status prune_det_sel(const float *energy, int32_t F, int32_t fra
 PRUNE_API prune_status prune_hx(const void *y, const int32_t *idx, const int32_t *c, int32_t F, int32_t B,
                       int32_t N, int32_t frames, const void *H, void *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free firing.  The paper has no counterpart: this entry point
+ * exists for callers of the library that cannot allocate device memory.
+ * ---------------------------------------------------------------------- */
+
+/* The fused firing loop (FIR, DET, SEL, HX_b, SINK; N < 64) over `frames`
+ * consecutive frames of one instance, for callers that cannot call
+ * cudaMalloc: code that enqueues work while a CUDA graph is being captured,
+ * real-time host threads that must not block in the allocator, deployments
+ * with a fixed device-memory budget.  It allocates nothing: inputs and
+ * outputs are the caller's, and its only scratch is a fixed array compiled
+ * into the library (every GPU that loads the library holds it, about 527 KB,
+ * until the process exits).  Results equal those of the graph entry points.
+ *   x        device, [frames][F*B] complex64, 16-byte aligned
+ *   hist     device, T-1 complex64 delay token before frame 0 (NULL = zeros)
+ *   taps     device, T complex64;  H device, [N][N] complex64
+ *   c        device, [frames] int32: selected blocks per frame
+ *   idx      device, [frames][F] int32: ascending selected indices (first c[k])
+ *   y        device, [frames][F*B] complex64, 16-byte aligned: compacted HX
+ *            output (first c[k]*B samples of each frame)
+ *   hist_out device, T-1 complex64 delay token after the last frame, or NULL;
+ *            must not alias hist
+ *   status   device, 4 uint32: zeroed by the call, then {code, actor, fifo,
+ *            frame} of a device-side failure (code 0 = success)
+ *   stream   cudaStream_t (NULL = legacy default stream); asynchronous
+ * Limits: at most 256 frames per call and frames * tiles <= 65536, tiles =
+ * ceil(F*B / TS) with TS the largest multiple of B not above 2048 (for
+ * F = 4096, B = 1024: 32 frames per call).  Beyond that, for N >= 64 or for
+ * a bad shape it returns PRUNE_EINVAL with a message in prune_last_error(NULL)
+ * and enqueues nothing.  The first call on a device looks up the device
+ * address of the scratch (once per device, with that device current); make
+ * that first call before any stream capture.  Every call shares the scratch
+ * and leaves its contents behind; each call clears what must start at zero,
+ * in stream order, so calls ordered on one stream are safe, while calls that
+ * can overlap on the GPU race on the scratch. */
+PRUNE_API prune_status prune_fire_frames_noalloc(const void *x, const void *hist, const void *taps,
+                                                 const void *H, int32_t F, int32_t B, int32_t T,
+                                                 int32_t N, int32_t frames, float tau, int32_t *c,
+                                                 int32_t *idx, void *y, void *hist_out,
+                                                 uint32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

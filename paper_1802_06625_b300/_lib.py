@@ -24,7 +24,8 @@ PRUNE_NUM_FIFOS = 8
 
 EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "prune_push_frames",
            "prune_run", "prune_sync", "prune_pull", "prune_peek", "prune_fifo_stats",
-           "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx")
+           "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx",
+           "prune_fire_frames_noalloc")
 
 
 class prune_graph_desc(ctypes.Structure):
@@ -72,6 +73,7 @@ def load(path: str | None = None):
         "prune_fir_energy": [P, P, P, I32, I32, I32, I32, P, P, P, P],
         "prune_det_sel": [P, I32, I32, ctypes.c_float, P, P, P],
         "prune_hx": [P, P, P, I32, I32, I32, I32, P, P, P],
+        "prune_fire_frames_noalloc": [P, P, P, P, I32, I32, I32, I32, I32, ctypes.c_float, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -30,7 +30,7 @@ struct DetSelParams {
   uint64_t cap_f4, cap_f5, cap_f6;
 };
 
-__global__ void __launch_bounds__(kDetThreads) det_sel_kernel(DetSelParams p) {
+static __global__ void __launch_bounds__(kDetThreads) det_sel_kernel(DetSelParams p) {
   __shared__ int warp_off[32];
   __shared__ int total_s;
   const int k = blockIdx.x;

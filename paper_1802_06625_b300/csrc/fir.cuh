@@ -141,7 +141,7 @@ __device__ __forceinline__ void fir_block_energies(const float2 (&acc)[kSPT], in
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kFirThreads) fir_energy_kernel(FirParams p) {
+static __global__ void __launch_bounds__(kFirThreads) fir_energy_kernel(FirParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TP = p.TP;
   const int win = TP - 1 + kFirTile;

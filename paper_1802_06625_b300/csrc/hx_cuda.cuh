@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kHxThreads) hx_cuda_kernel(HxParams p) {
 }
 
 // Any N (no register blocking): H in shared memory after the block.
-__global__ void __launch_bounds__(kHxThreads) hx_cuda_generic_kernel(HxParams p) {
+static __global__ void __launch_bounds__(kHxThreads) hx_cuda_generic_kernel(HxParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *xs = reinterpret_cast<float2 *>(smem_raw);
   float2 *hs = xs + p.B;

@@ -48,7 +48,7 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows)
 }
 
 // R (scaled) split into hi / lo FP16 in the shared-memory layout.
-__global__ void hx_tc_prepare_b_kernel(const float2 *H, uint16_t *bops) {
+static __global__ void hx_tc_prepare_b_kernel(const float2 *H, uint16_t *bops) {
   const int n = blockIdx.x, k = threadIdx.x;  // 128 x 128
   const int i = n >> 1, kk = k >> 1;
   const float2 h = H[i * kTcNc + kk];
@@ -168,7 +168,7 @@ struct HxTcParams {
   uint64_t timeout_ns;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams tp) {
+static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const HxParams &p = tp.p;
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &

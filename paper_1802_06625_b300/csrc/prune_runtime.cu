@@ -67,6 +67,9 @@ bool shape_ok(int32_t F, int32_t B, int32_t T, int32_t N, std::string *why) {
 
 }  // namespace
 
+// Message for prune_last_error(NULL) from entry points without a graph.
+void prune_set_create_error(const std::string &m) { t_create_error = m; }
+
 struct prune_graph {
   prune_graph_desc d{};
   int dev = 0;
