@@ -41,7 +41,8 @@ UNIT = "Msamples/s"
 # FP32 lanes x 2 flop x 2.032 GHz.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 KIND_NAMES = {0: "f0_push_kernel", 1: "fir_energy_kernel", 2: "det_sel_kernel", 3: "hx_cuda_kernel",
-              4: "hx_tc_kernel", 5: "firing_loop_kernel"}
+              4: "hx_tc_kernel", 5: "firing_loop_kernel", 6: "firing_loop_tc_kernel"}
+NKINDS = 7
 
 
 def measured_peaks():
@@ -208,18 +209,29 @@ def run_ours(args, w):
               stream=stream, device=local)
     L = w.F * w.B
 
+    actors, cuda_cores = args.path == "actors", args.path == "cuda_cores"
+
     def step():
         for k in range(0, frames, C):
             m = min(C, frames - k)
             g.push(x[k:k + m], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
-            g.run(actors=args.actors)
+            g.run(actors=actors, cuda_cores=cuda_cores)
         g.discard()
 
     for _ in range(args.warmup):
         step()
     g.sync()
+    # selected blocks per step (the same every step: the same frames)
+    for k in range(0, frames, C):
+        m = min(C, frames - k)
+        g.push(x[k:k + m], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+        g.run(actors=actors, cuda_cores=cuda_cores)
+    recs = (_lib.prune_frame_out * frames)()
+    nrec = ctypes.c_int32()
+    _lib.check(_lib.lib().prune_pull(g.h, recs, frames, ctypes.byref(nrec), _lib.PRUNE_MEM_DISCARD), g.h)
+    selected_blocks = sum(recs[i].c for i in range(nrec.value))
     g.profile(True)
-    for kind in range(6):
+    for kind in range(NKINDS):
         g.kernel_times(kind, reset=True)
 
     barrier(ws)
@@ -234,7 +246,7 @@ def run_ours(args, w):
         torch.cuda.synchronize(dev)
     barrier(ws)
     ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
-    times = {k: g.kernel_times(k, reset=True) for k in range(6)}
+    times = {k: g.kernel_times(k, reset=True) for k in range(NKINDS)}
     g.profile(False)
     launches = sum(n for _, n in times.values())
     samples = sum_over_ranks(float(args.steps * frames * L), ws, dev)
@@ -245,17 +257,29 @@ def run_ours(args, w):
     peaks = measured_peaks()
     runs = args.steps * ((frames + C - 1) // C)
     roof = None
+    sel_frac = selected_blocks / float(frames * w.F)
     if kn:
         avg_s = kms / kn / 1e3
-        frames_per_launch = args.steps * frames / kn if kind in (1, 2, 5) else args.steps * frames / kn
-        if kind == 1:      # FIR: T complex MACs = 8T flop per sample (CUDA-core FP32)
-            work = 8.0 * w.T * L * frames_per_launch
+        frames_per_launch = args.steps * frames / kn
+        samples = L * frames_per_launch
+        if kind in (1, 5):  # CUDA-core FIR (+HX): 8T (+8N per selected sample) FP32 flop per sample
+            work = (8.0 * w.T + (8.0 * w.N * sel_frac if kind == 5 else 0.0)) * samples
             roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz"}
-        else:              # HBM-bound kernels: algorithmic bytes per launch
-            nbytes = 16.0 * L * frames_per_launch
+        else:               # bytes the path must move: frames in, selected blocks + indices out
+            nbytes = 8.0 * samples + (8.0 * w.B + 4.0) * w.F * sel_frac * frames_per_launch
+            if kind == 2:
+                nbytes = 8.0 * w.F * frames_per_launch
             roof = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "peak_source": "measured" if not peaks.get("fallback") else "fallback"}
+            if kind == 6:   # tensor pipe: split-FP16 3-pass FIR (ns shifts) + HX on selected rows
+                ns = 1 + (w.T - 1 + 31) // 32
+                tflop = samples * (3 * ns * 2 * 64 * 64 * 2 / 32 + sel_frac * 3 * 2 * 64 * 64 / 32 * 2) / 2
+                peak_t = peaks.get("bf16_tflops_sustained", 1400.0)
+                roof["tensor"] = {"achieved": tflop / avg_s / 1e12, "peak": peak_t, "unit": "TFLOP/s",
+                                  "frac": tflop / avg_s / 1e12 / peak_t,
+                                  "note": "FP16 MMA work incl. the 3 split passes; peak = measured BF16 sustained "
+                                          "(FP16 has the same nominal rate)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = args.traffic
         roof["kernel"] = KIND_NAMES[kind]
@@ -267,7 +291,8 @@ def run_ours(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded SplitMix64 + Box-Muller, generated on device)",
             "config": {"workload": w.name, "F": w.F, "B": w.B, "T": w.T, "N": w.N, "tau": w.tau,
-                       "frames_per_step": frames, "C": C, "path": "actors" if args.actors else "firing_loop",
+                       "frames_per_step": frames, "C": C, "path": args.path,
+                       "selected_fraction": sel_frac,
                        "l2": "inputs larger than L2 (%.1f GiB per step), no flush" % (frames * L * 8 / 2**30),
                        "parallelism": f"instance-sharded x{ws}" if ws > 1 else "single instance"},
             "roofline": roof, "gpu_launches": launches,
@@ -346,7 +371,9 @@ def main():
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default: the workload's)")
     ap.add_argument("--C", type=int, default=3, help="buffering constant of eq. (2)")
-    ap.add_argument("--actors", action="store_true", help="one kernel per actor instead of the fused loop")
+    ap.add_argument("--path", default="fused", choices=["fused", "cuda_cores", "actors"],
+                    help="fused loop (tensor cores where the shape allows), fused loop on CUDA cores, "
+                         "or one kernel per actor")
     ap.add_argument("--e2e-frames", type=int, default=48)
     ap.add_argument("--cpu-frames", type=int, default=8)
     ap.add_argument("--ref-frames", type=int, default=1)

@@ -94,6 +94,9 @@ enum {
   PRUNE_RUN_SYNC = 1,    /* return once they completed (device status checked) */
   PRUNE_RUN_ACTORS = 2,  /* fire one kernel per actor instead of the fused firing
                             loop (same results; FIFOs f2/f3 materialised in HBM) */
+  PRUNE_RUN_CUDA_CORES = 8, /* fire the fused loop with FIR and HX_b on CUDA cores even
+                            where the tensor-core loop applies (N = 32, B dividing
+                            4096 and a multiple of 32, T <= 129) */
   PRUNE_RUN_DEVICE_RULE = 4 /* let the device alone enforce FIR's firing rule on f0:
                             the host does not bound the run by the frames pushed,
                             so frames may be pushed later from another stream; a
@@ -206,7 +209,8 @@ PRUNE_API prune_status prune_fifo_capacity_of(prune_graph *g, int32_t fifo, int6
 /* Per-kernel timing for measurement.  With enable != 0 the graph records a
  * CUDA event pair around every kernel it launches on its stream; kernel
  * kinds: 0 = f0 push commit, 1 = FIR(+energy), 2 = DET+SEL, 3 = HX on CUDA
- * cores, 4 = HX on tensor cores, 5 = fused firing loop.  prune_kernel_times
+ * cores, 4 = HX on tensor cores, 5 = fused firing loop on CUDA cores, 6 = fused
+ * firing loop on tensor cores.  prune_kernel_times
  * waits for the graph, returns the summed device milliseconds and launch
  * count of one kind since the last reset, and resets that kind if reset != 0. */
 PRUNE_API prune_status prune_profile(prune_graph *g, int32_t enable);

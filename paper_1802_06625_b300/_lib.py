@@ -19,7 +19,7 @@ PRUNE_ETIMEOUT, PRUNE_ECUDA, PRUNE_EBUSY, PRUNE_EDEVICE = 4, 5, 6, 7
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EAGAIN", 4: "ETIMEOUT", 5: "ECUDA",
                 6: "EBUSY", 7: "EDEVICE"}
 PRUNE_MEM_HOST, PRUNE_MEM_DEVICE, PRUNE_MEM_DEVICE_BORROW, PRUNE_MEM_DISCARD = 0, 1, 2, 3
-PRUNE_RUN_ASYNC, PRUNE_RUN_SYNC, PRUNE_RUN_ACTORS, PRUNE_RUN_DEVICE_RULE = 0, 1, 2, 4
+PRUNE_RUN_ASYNC, PRUNE_RUN_SYNC, PRUNE_RUN_ACTORS, PRUNE_RUN_DEVICE_RULE, PRUNE_RUN_CUDA_CORES = 0, 1, 2, 4, 8
 PRUNE_NUM_FIFOS = 8
 
 EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "prune_push_frames",

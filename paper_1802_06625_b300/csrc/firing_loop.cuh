@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(kFirThreads) firing_loop_kernel(LoopParams p) 
     if (tid == 0) {
       __threadfence();
       const uint32_t old = atomicAdd(&p.done[fslot], 1u);
-      if ((old + 1u) % static_cast<uint32_t>(f.tiles) == 0u) {
+      if (old + 1u == static_cast<uint32_t>(f.tiles)) {
+        p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
         const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
         const uint32_t c = static_cast<uint32_t>(w);
         p.rec_c[rs] = static_cast<int32_t>(c);

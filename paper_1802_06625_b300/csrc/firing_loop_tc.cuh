@@ -1,0 +1,430 @@
+// Fused firing loop on tcgen05 tensor cores (N = 32): FIR, DET, SEL, HX_b and
+// SINK per tile of 4096 outputs, with FIR and HX_b as tensor-core GEMMs.
+//
+// FIR as a block-Toeplitz GEMM.  A tile is 128 rows of 32 consecutive outputs;
+// X_j is the j-th 32-sample chunk of the input from the tile start.  With
+//   G_s[i][u] = h[i - u + 32 s]   (zero outside 0 <= i - u + 32 s < T),
+// the outputs of row m are  y_m = sum_{s=0}^{S} G_s X_{m-s},  S = ceil((T-1)/32):
+// this is the convolution y[n] = sum_t h[t] x[n-t] regrouped, nothing is
+// approximated.  Each G_s is a 32 x 32 complex matrix used in its real form
+// (64 x 64, as for HX), so a shift is one 128 x 64 x 64 real GEMM whose A
+// operand is the chunk array itself, started S - s rows later.  The chunk
+// array is stored once in the K-major 128-byte-swizzle layout; a start that
+// is not on an 8-row boundary is given to the tensor core through the
+// descriptor's base-offset field (the row phase of the swizzle pattern).
+//
+// Accuracy: operands split a = a_hi + a_lo into FP16 and three products
+// (hi hi, hi lo, lo hi) accumulated in FP32 in tensor memory, ~2^-22
+// relative; the tap and H operands are pre-scaled by 2^8.
+//
+// HX_b (N = 32): a FIR output row is exactly one row of N samples of a
+// block, so the selected blocks' FIR rows (read from TMEM) are compacted into
+// the A operand of a second 128 x 64 x 64 GEMM with the real form of H.
+//
+// Control: block energies from the FIR accumulators, v[b] = E_b > tau, warp
+// ballot compaction in the tile and the warp-parallel decoupled look-back of
+// the CUDA-core firing loop across tiles; the last tile of a frame writes the
+// SINK record and books the FIFO counters in frame order.  All waits are
+// bounded; tensor memory is freed on every path.
+#pragma once
+#include "firing_loop.cuh"
+#include "hx_tc.cuh"
+
+namespace prune {
+
+constexpr int kTR = 32;                  // complex outputs per GEMM row
+constexpr int kTRows = 128;              // GEMM rows per tile (M)
+constexpr int kTTile = kTR * kTRows;     // 4096 outputs per tile
+constexpr int kTMaxShifts = 5;           // T <= 4 * 32 + 1
+constexpr int kTARows = 136;             // chunk array rows (128 + halo, 8-aligned)
+constexpr uint32_t kTOpBytes = 64 * 128; // one 64 x 64 FP16 operand (8 KB)
+constexpr uint32_t kTIdescN64 = (1u << 4) | (static_cast<uint32_t>(64 >> 3) << 17) |
+                                (static_cast<uint32_t>(kTRows >> 4) << 24);
+constexpr float kTScale = 256.f;
+
+__host__ __device__ inline int tc_shifts(int T) { return 1 + (T - 1 + kTR - 1) / kTR; }
+
+__host__ inline bool tc_loop_supported(int N, int B, int T) {
+  return N == 32 && B % kTR == 0 && B <= kTTile && kTTile % B == 0 && T <= (kTMaxShifts - 1) * kTR + 1;
+}
+
+__host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
+  const int ns = tc_shifts(T);
+  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes + 2 * kTARows * 128 + 4096;
+}
+
+// Operand elements: ns shifts x {hi, lo} x 64 x 64 for FIR, {hi, lo} x 64 x 64 for HX.
+__host__ inline size_t tc_fir_ops_elems(int T) { return static_cast<size_t>(tc_shifts(T)) * 2 * 64 * 64; }
+__host__ inline size_t tc_hx_ops_elems() { return 2 * 64 * 64; }
+
+// Real form of a 32 x 32 complex matrix M (element getter) at row n, column k.
+__device__ __forceinline__ float real_form(float2 g, int n, int k) {
+  if ((n & 1) == 0) return (k & 1) == 0 ? g.x : -g.y;
+  return (k & 1) == 0 ? g.y : g.x;
+}
+
+__device__ __forceinline__ void store_split(uint16_t *ops, uint32_t half_elems, int n, int k, float v) {
+  v *= kTScale;
+  const __half hi = __float2half_rn(v);
+  const __half lo = __float2half_rn(v - __half2float(hi));
+  const uint32_t off = sw128_off(n, k, 64) >> 1;
+  ops[off] = __half_as_ushort(hi);
+  ops[half_elems + off] = __half_as_ushort(lo);
+}
+
+// FIR operands: shift s, real row n < 64 (output 2i+a), real column k < 64.
+static __global__ void tc_prepare_fir_kernel(const float2 *taps, int T, uint16_t *ops) {
+  const int s = blockIdx.y, n = blockIdx.x, k = threadIdx.x;
+  const int i = n >> 1, u = k >> 1;
+  const int t = i - u + kTR * s;
+  const float2 g = (t >= 0 && t < T) ? taps[t] : make_float2(0.f, 0.f);
+  store_split(ops + static_cast<size_t>(s) * 2 * 64 * 64, 64 * 64, n, k, real_form(g, n, k));
+}
+
+// HX operands: real form of H (32 x 32 complex).
+static __global__ void tc_prepare_hx_kernel(const float2 *H, uint16_t *ops) {
+  const int n = blockIdx.x, k = threadIdx.x;
+  store_split(ops, 64 * 64, n, k, real_form(H[(n >> 1) * kTR + (k >> 1)], n, k));
+}
+
+__host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const float2 *H, uint16_t *fir_ops,
+                                           uint16_t *hx_ops, cudaStream_t s) {
+  tc_prepare_fir_kernel<<<dim3(64, tc_shifts(T)), 64, 0, s>>>(taps, T, fir_ops);
+  tc_prepare_hx_kernel<<<64, 64, 0, s>>>(H, hx_ops);
+  return cudaGetLastError();
+}
+
+// Descriptor for a K-major 128-byte-swizzle operand whose start may sit on
+// any 128-byte row: the base offset carries the row phase of the pattern.
+__device__ __forceinline__ uint64_t umma_desc_rows(uint32_t saddr) {
+  return umma_desc_sw128(saddr) | (static_cast<uint64_t>((saddr >> 7) & 7u) << 49);
+}
+
+struct TcLoopParams {
+  LoopParams lp;
+  const uint16_t *fir_ops;
+  const uint16_t *hx_ops;
+  int32_t ns;
+};
+
+__device__ __forceinline__ uint4 split_pack8(const float *v, bool lo) {
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __half h0 = __float2half_rn(v[2 * e]), h1 = __float2half_rn(v[2 * e + 1]);
+    __half a = h0, b = h1;
+    if (lo) {
+      a = __float2half_rn(v[2 * e] - __half2float(h0));
+      b = __float2half_rn(v[2 * e + 1] - __half2float(h1));
+    }
+    w[e] = static_cast<uint32_t>(__half_as_ushort(a)) | (static_cast<uint32_t>(__half_as_ushort(b)) << 16);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopParams tp) {
+  extern __shared__ unsigned char smem_raw[];
+  const LoopParams &p = tp.lp;
+  const FirParams &f = p.f;
+  const int ns = tp.ns, S = ns - 1;
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *bfir = base;
+  unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
+  unsigned char *ahi = bhx + 2 * kTOpBytes;
+  unsigned char *alo = ahi + kTARows * 128;
+  unsigned char *misc = alo + kTARows * 128;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);               // [2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 16);
+  int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 20);
+  int32_t *s_cnt = reinterpret_cast<int32_t *>(misc + 24);
+  long long *s_prefix = reinterpret_cast<long long *>(misc + 32);
+  unsigned long long *s_ticket = reinterpret_cast<unsigned long long *>(misc + 40);
+  int32_t *s_rank = reinterpret_cast<int32_t *>(misc + 64);          // [128] (blocks per tile <= 128)
+  float *eth = reinterpret_cast<float *>(misc + 64 + 512);           // [256]
+  float *Et = eth + 256;                                              // [128]
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // constant operands, once per CTA
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(tp.fir_ops);
+    uint4 *dst = reinterpret_cast<uint4 *>(bfir);
+    for (int q = tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += 256) dst[q] = src[q];
+    const uint4 *hsrc = reinterpret_cast<const uint4 *>(tp.hx_ops);
+    uint4 *hdst = reinterpret_cast<uint4 *>(bhx);
+    for (int q = tid; q < static_cast<int>(2 * kTOpBytes / 16); q += 256) hdst[q] = hsrc[q];
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(128u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t ph0 = 0, ph1 = 0;
+  bool failed = false;
+
+  const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
+  const int qd = warp & 3, hf = warp >> 2;
+  const int m = qd * 32 + lane;  // tile row owned in the epilogues
+  for (;;) {
+    if (tid == 0) {
+      const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
+      *s_ticket = ld_volatile_u32(&p.ls->abort) ? ~0ull : tk;
+    }
+    __syncthreads();
+    const unsigned long long t = *s_ticket;
+    if (t >= total) break;
+    const int k = static_cast<int>(t / f.tiles);
+    const int tile = static_cast<int>(t % f.tiles);
+    const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
+    const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
+    const int nv = static_cast<int>(min(static_cast<int64_t>(kTTile), f.L - s0));
+    const int rows_valid = nv / kTR;
+
+    // firing rule of FIR on f0 (device counter, bounded wait)
+    if (tid == 0) {
+      const uint64_t need = (seq + 1) * static_cast<uint64_t>(f.F);
+      const bool ok = bounded_wait(p, [&] { return ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]) >= need; },
+                                   kActFir, 0, seq);
+      *s_cnt = ok ? 0 : -1;
+    }
+    __syncthreads();
+    if (*s_cnt < 0) break;
+
+    // ---- FIR A operand: chunk array rows j + S for chunks j in [-S, 128)
+    const float2 *cur = f.src.frame(k);
+    const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
+    for (int q = tid; q < (kTRows + S) * 8; q += 256) {
+      const int row = q >> 3, pc = q & 7;
+      const int j = row - S;
+      const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
+      float v[8];
+      if (j >= 0) {
+        if (kTR * j + 4 * pc < nv) {
+          const float4 *src = reinterpret_cast<const float4 *>(cur + pos0);
+          const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
+          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+          v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t pos = pos0 + e;
+          const int64_t d = s0 - pos;
+          float2 x = make_float2(0.f, 0.f);
+          if (d <= f.T - 1) {
+            if (pos >= 0) x = cur[pos];
+            else if (prev) x = prev[f.L + pos];
+            else if (f.hist) x = f.hist[f.T - 1 + pos];
+          }
+          v[2 * e] = x.x;
+          v[2 * e + 1] = x.y;
+        }
+      }
+      const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+      *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v, false);
+      *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v, true);
+    }
+    if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
+      for (int i = tid; i < f.T - 1; i += 256) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+
+    // ---- FIR GEMM: ns shifts x 3 passes x 4 K-steps of 128 x 64 x 16
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), b0 = smem_u32(bfir);
+      for (int s = 0; s < ns; ++s) {
+        const uint32_t arow = static_cast<uint32_t>(S - s) * 128u;
+        const uint32_t pa[3] = {ah + arow, ah + arow, al + arow};
+        const uint32_t bh = b0 + static_cast<uint32_t>(2 * s) * kTOpBytes, bl = bh + kTOpBytes;
+        const uint32_t pb[3] = {bh, bl, bh};
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_f16(tmem, umma_desc_rows(pa[pass] + ks * 32), umma_desc_rows(pb[pass] + ks * 32), kTIdescN64,
+                     (s > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&mbar[0]));
+    }
+    if (!mbar_wait_bounded(smem_u32(&mbar[0]), ph0, p.timeout_ns)) {
+      if (tid == 0) report_error(p.status, kDevTimeout, kActFir, 2, seq);
+      *s_flag = 1;
+    }
+    ph0 ^= 1u;
+    __syncthreads();
+    if (*s_flag) { failed = true; break; }
+    tc_fence_after();
+
+    // ---- DET: FIR outputs of row m, complex columns [16 hf, 16 hf + 16)
+    float y[32];
+    {
+      float t16[16];
+      tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(hf * 32), t16);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) y[e] = t16[e];
+      tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(hf * 32 + 16), t16);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) y[16 + e] = t16[e];
+      tmem_ld_wait();
+    }
+    float e = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      y[i] *= 1.f / kTScale;
+      e = fmaf(y[i], y[i], e);
+    }
+    eth[m * 2 + hf] = m < rows_valid ? e : 0.f;
+    __syncthreads();
+    const int rpb = f.B / kTR;  // rows per block
+    const int nb = nv / f.B;
+    if (tid < nb) {
+      float E = 0.f;
+      for (int r = 0; r < rpb; ++r) E += eth[(tid * rpb + r) * 2] + eth[(tid * rpb + r) * 2 + 1];
+      Et[tid] = E;
+      if (f.energy) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + tid] = E;
+    }
+    __syncthreads();
+    // ---- SEL inside the tile: stable ballot compaction
+    if (warp == 0) {
+      int cnt = 0;
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        const bool v = b < nb && Et[b] > p.tau;
+        const unsigned msk = __ballot_sync(0xffffffffu, v);
+        if (b < nb) s_rank[b] = v ? cnt + __popc(msk & ((1u << lane) - 1u)) : -1;
+        cnt += __popc(msk);
+      }
+      if (lane == 0) *s_cnt = cnt;
+    }
+    __syncthreads();
+    const int cnt = *s_cnt;
+    // selected rows become rows of the HX A operand (the FIR operand area is free)
+    if (m < rows_valid) {
+      const int rk = s_rank[m / rpb];
+      if (rk >= 0) {
+        const int hrow = rk * rpb + m % rpb;
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) {
+          const uint32_t off = static_cast<uint32_t>(hrow) * 128u +
+                               (static_cast<uint32_t>((4 * hf + pp) ^ (hrow & 7)) << 4);
+          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(y + 8 * pp, false);
+          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(y + 8 * pp, true);
+        }
+      }
+    }
+    // ---- SEL across tiles: decoupled look-back
+    const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
+    if (warp == 0) {
+      const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
+      if (lane == 0) *s_prefix = pr;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    const long long prefix = *s_prefix;
+    if (prefix < 0) { failed = true; break; }
+    if (prefix + cnt > f.F) {
+      if (tid == 0) {
+        report_error(p.status, kDevInvariant, kActSel, 6, seq);
+        atomicExch(&p.ls->abort, 1u);
+      }
+      failed = true;
+      break;
+    }
+    const int64_t rs = p.rslot.slot(k);
+    if (tid < nb && s_rank[tid] >= 0) p.rec_idx[rs * f.F + prefix + s_rank[tid]] = static_cast<int32_t>(s0 / f.B) + tid;
+
+    // ---- HX_b GEMM on the compacted rows, then the SINK payload
+    if (cnt > 0) {
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), bh = smem_u32(bhx), bl = bh + kTOpBytes;
+        const uint32_t pa[3] = {ah, ah, al}, pb[3] = {bh, bl, bh};
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_f16(tmem + 64u, umma_desc_rows(pa[pass] + ks * 32), umma_desc_rows(pb[pass] + ks * 32), kTIdescN64,
+                     (pass > 0 || ks > 0) ? 1u : 0u);
+        umma_commit(smem_u32(&mbar[1]));
+      }
+      if (!mbar_wait_bounded(smem_u32(&mbar[1]), ph1, p.timeout_ns)) {
+        if (tid == 0) report_error(p.status, kDevTimeout, kActHx, 7, seq);
+        *s_flag = 1;
+      }
+      ph1 ^= 1u;
+      __syncthreads();
+      if (*s_flag) { failed = true; break; }
+      tc_fence_after();
+      float o[32];
+      {
+        float t16[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + 64u + static_cast<uint32_t>(hf * 32), t16);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[i] = t16[i];
+        tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + 64u + static_cast<uint32_t>(hf * 32 + 16), t16);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[16 + i] = t16[i];
+        tmem_ld_wait();
+      }
+      if (m < cnt * rpb) {
+        float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
+                                                 (m % rpb) * kTR + hf * 16);
+        const float sc = 1.f / kTScale;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          dst[i] = make_float4(o[4 * i] * sc, o[4 * i + 1] * sc, o[4 * i + 2] * sc, o[4 * i + 3] * sc);
+      }
+    }
+
+    // ---- frame completion: the last tile to finish writes the SINK record
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const uint32_t old = atomicAdd(&p.done[fslot], 1u);
+      if (old + 1u == static_cast<uint32_t>(f.tiles)) {
+        p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
+        const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
+        p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
+        p.rec_frame[rs] = static_cast<int64_t>(seq);
+        __threadfence();
+        st_release_u64(&p.ready[fslot], seq + 1);
+        __threadfence();
+        drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames);
+      }
+    }
+  }
+
+  // leave: let MMAs in flight land (bounded) before freeing tensor memory
+  if (failed) {
+    mbar_wait_bounded(smem_u32(&mbar[0]), ph0 ^ 1u, p.timeout_ns);
+    mbar_wait_bounded(smem_u32(&mbar[1]), ph1 ^ 1u, p.timeout_ns);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+  }
+}
+
+}  // namespace prune

@@ -21,6 +21,7 @@
 #include "hx_cuda.cuh"
 #include "firing_loop.cuh"
 #include "hx_tc.cuh"
+#include "firing_loop_tc.cuh"
 
 using namespace prune;
 
@@ -100,6 +101,8 @@ struct prune_graph {
   unsigned long long ticket_base = 0;
   uint64_t timeout_ns = 2000000000ull;
   uint16_t *hx_b_ops = nullptr;       // tcgen05 B operands (N >= 64)
+  uint16_t *tc_fir_ops = nullptr;     // tensor-core firing loop: FIR tap operands
+  uint16_t *tc_hx_ops = nullptr;      //   and the real form of H
   int64_t cap[PRUNE_NUM_FIFOS] = {};
   // optional per-kernel event timing
   bool profile = false;
@@ -245,7 +248,7 @@ cudaError_t launch_hx_cuda(const HxParams &p, int grid, cudaStream_t s) {
 
 }  // namespace
 
-static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n);
+static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int32_t flags);
 
 static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
   const prune_graph_desc &d = g->d;
@@ -317,7 +320,7 @@ static cudaError_t launch_loop_nt(const LoopParams &lp, int sms, size_t smem, cu
   return cudaGetLastError();
 }
 
-static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n) {
+static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int32_t flags) {
   const prune_graph_desc &d = g->d;
   const int64_t T1 = std::max(d.T - 1, 1);
   LoopParams lp{};
@@ -338,6 +341,34 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n) {
   lp.ls = g->loop; lp.ticket_base = g->ticket_base; lp.timeout_ns = g->timeout_ns;
   lp.ctr = g->ctr; lp.status = g->status;
   for (int i = 0; i < 8; ++i) lp.cap[i] = static_cast<uint64_t>(g->cap[i]);
+  if (g->tc_fir_ops && !(flags & PRUNE_RUN_CUDA_CORES)) {
+    // FIR and HX_b on tensor cores: tiles of 4096 outputs
+    TcLoopParams tp{};
+    tp.lp = lp;
+    tp.lp.f.TS = kTTile;
+    tp.lp.f.tiles = static_cast<int32_t>((g->L + kTTile - 1) / kTTile);
+    tp.fir_ops = g->tc_fir_ops;
+    tp.hx_ops = g->tc_hx_ops;
+    tp.ns = tc_shifts(d.T);
+    const size_t smem = tc_loop_smem_bytes(d.T);
+    cudaError_t e = cudaFuncSetAttribute(firing_loop_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    int occ = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, firing_loop_tc_kernel, 256, smem);
+    if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop: ") + cudaGetErrorString(e));
+    occ = std::max(occ, 1);
+    const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
+    const int grid = static_cast<int>(std::min<unsigned long long>(ttotal, static_cast<unsigned long long>(g->sms) * occ));
+    {
+      KTimer kt(g, 6);
+      firing_loop_tc_kernel<<<grid, 256, smem, g->stream>>>(tp);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop launch: ") + cudaGetErrorString(e));
+    g->ticket_base += ttotal + static_cast<unsigned long long>(grid);
+    return PRUNE_OK;
+  }
   const unsigned long long total = static_cast<unsigned long long>(n) * g->tiles;
   int grid = 0;
   cudaError_t e;
@@ -473,6 +504,10 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
   if (N >= 64 && hx_tc_supported(N)) {
     if ((s = galloc(g, &g->hx_b_ops, hx_tc_b_elems(N)))) return bail(s);
   }
+  if (tc_loop_supported(N, desc->B, T)) {
+    if ((s = galloc(g, &g->tc_fir_ops, tc_fir_ops_elems(T))) || (s = galloc(g, &g->tc_hx_ops, tc_hx_ops_elems())))
+      return bail(s);
+  }
   auto upload = [&](void *dst, const void *src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream) == cudaSuccess;
   };
@@ -488,6 +523,7 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
             cudaMemsetAsync(g->ready, 0, sizeof(uint64_t) * C, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->rec_c, 0, sizeof(int32_t) * out_cap, g->stream) == cudaSuccess;
   if (ok && g->hx_b_ops) ok = hx_tc_prepare_b(g->H, N, g->hx_b_ops, g->stream) == cudaSuccess;
+  if (ok && g->tc_fir_ops) ok = tc_prepare_ops(g->taps, T, g->H, g->tc_fir_ops, g->tc_hx_ops, g->stream) == cudaSuccess;
   // the initial delay token of f1 is present from the start (Q = 1)
   if (ok) {
     const uint64_t init[3] = {0, 0, 1};
@@ -555,7 +591,7 @@ prune_status prune_run(prune_graph *g, int32_t max_frames, int32_t *n_fired, int
   if (n > 0) {
     prune_status s;
     if ((flags & PRUNE_RUN_ACTORS) || !loop_supported(g->d.N)) s = run_actor_kernels(g, g->fired, n);
-    else s = run_firing_loop(g, g->fired, n);
+    else s = run_firing_loop(g, g->fired, n, flags);
     if (s != PRUNE_OK) return s;
     g->fired += n;
     g->runs++;

@@ -68,9 +68,10 @@ class Graph:
         check(_lib.lib().prune_push_frames(self.h, x.data_ptr(), n, mem), self.h)
 
     # -- all actors
-    def run(self, max_frames=1 << 30, sync=False, actors=False) -> int:
+    def run(self, max_frames=1 << 30, sync=False, actors=False, cuda_cores=False) -> int:
         n = ctypes.c_int32()
-        flags = (_lib.PRUNE_RUN_SYNC if sync else 0) | (_lib.PRUNE_RUN_ACTORS if actors else 0)
+        flags = ((_lib.PRUNE_RUN_SYNC if sync else 0) | (_lib.PRUNE_RUN_ACTORS if actors else 0)
+                 | (_lib.PRUNE_RUN_CUDA_CORES if cuda_cores else 0))
         check(_lib.lib().prune_run(self.h, max_frames, ctypes.byref(n), flags), self.h)
         if sync:
             self._borrowed.clear()
@@ -121,7 +122,7 @@ class Graph:
             out[f"f{f}"] = (w.value, r.value, p.value)
         return out
 
-    KIND_PUSH, KIND_FIR, KIND_DETSEL, KIND_HX_CUDA, KIND_HX_TC, KIND_LOOP = range(6)
+    KIND_PUSH, KIND_FIR, KIND_DETSEL, KIND_HX_CUDA, KIND_HX_TC, KIND_LOOP, KIND_LOOP_TC = range(7)
 
     def profile(self, enable=True):
         check(_lib.lib().prune_profile(self.h, 1 if enable else 0), self.h)

@@ -19,8 +19,16 @@ def G():
     return graph
 
 
-def run_graph(G, w, x, actors=False, C=None, out_frames=0, mem=None, chunk=None):
-    """Push, fire and pull all frames of x [n, F, B]; returns records, stats."""
+PATHS = ("fused", "cuda_cores", "actors")
+
+
+def run_graph(G, w, x, actors=False, C=None, out_frames=0, mem=None, chunk=None, path=None):
+    """Push, fire and pull all frames of x [n, F, B]; returns records, stats.
+    path: "fused" (tensor-core loop where the shape allows it, else the
+    CUDA-core loop), "cuda_cores" (fused loop on CUDA cores) or "actors"."""
+    if path is not None:
+        actors = path == "actors"
+    cuda_cores = path == "cuda_cores"
     C = C or w.C
     g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=C, out_frames=out_frames)
     n = x.shape[0]
@@ -30,7 +38,7 @@ def run_graph(G, w, x, actors=False, C=None, out_frames=0, mem=None, chunk=None)
     while k < n:
         m = min(chunk or C, n - k)
         g.push(xd[k:k + m], mem=mem)
-        assert g.run(actors=actors) == m
+        assert g.run(actors=actors, cuda_cores=cuda_cores) == m
         recs += g.pull()
         k += m
     stats = g.fifo_stats()
@@ -60,11 +68,11 @@ def check_against_oracle(w, x_np, recs, stats=None, caps=None):
     return r, worst, bands
 
 
-@pytest.mark.parametrize("actors", [False, True])
-def test_plain_small_workload_100_frames(G, actors):
+@pytest.mark.parametrize("path", PATHS)
+def test_plain_small_workload_100_frames(G, path):
     w = synth.PLAIN_SMALL
     x = w.frames_tensor(0, w.frames)
-    recs, stats, caps = run_graph(G, w, x.cuda(), actors=actors)
+    recs, stats, caps = run_graph(G, w, x.cuda(), path=path)
     r, worst, bands = check_against_oracle(w, x.numpy(), recs, stats, caps)
     assert bands == 0
     assert np.all(r.c == 16)
@@ -77,9 +85,33 @@ def test_plain_small_workload_100_frames(G, actors):
 def test_ragged_and_degenerate_shapes(G, F, B, T, N, C, frames):
     w = synth.PlainWorkload("t", F=F, B=B, T=T, N=N, frames=frames, tau=4.0 * B, seed=F + B + T, p=0.4, C=C)
     x = w.frames_tensor(0, frames)
-    for actors in (False, True):
-        recs, stats, caps = run_graph(G, w, x.cuda(), actors=actors, C=C)
+    for path in PATHS:
+        recs, stats, caps = run_graph(G, w, x.cuda(), C=C, path=path)
         check_against_oracle(w, x.numpy(), recs, stats, caps)
+
+
+# Shapes of the tensor-core firing loop (N = 32, B | 4096): 1 to 5 tap
+# shifts, B from 32 to 2048, ragged last tiles, single-frame runs.
+@pytest.mark.parametrize("F,B,T,N,C,frames", [(64, 256, 64, 32, 3, 4), (5, 1024, 64, 32, 3, 5),
+                                              (9, 512, 128, 32, 2, 3), (3, 2048, 1, 32, 3, 4),
+                                              (130, 32, 33, 32, 3, 3), (37, 128, 17, 32, 4, 6),
+                                              (7, 1024, 129, 32, 1, 3), (300, 256, 64, 32, 3, 3)])
+@pytest.mark.parametrize("path", PATHS)
+def test_tensor_core_loop_shapes(G, F, B, T, N, C, frames, path):
+    w = synth.PlainWorkload("t", F=F, B=B, T=T, N=N, frames=frames, tau=4.0 * B, seed=F * 7 + B + T, p=0.45, C=C)
+    x = w.frames_tensor(0, frames)
+    recs, stats, caps = run_graph(G, w, x.cuda(), C=C, path=path)
+    check_against_oracle(w, x.numpy(), recs, stats, caps)
+
+
+def test_paths_agree_on_control_and_within_tolerance(G):
+    w = synth.PlainWorkload("t", F=512, B=1024, T=64, N=32, frames=6, tau=4096.0, seed=21, p=None)
+    x = w.frames_tensor(0, 6).cuda()
+    out = {path: run_graph(G, w, x, path=path)[0] for path in PATHS}
+    for a, b in zip(out["fused"], out["cuda_cores"]):
+        assert a[1] == b[1] and np.array_equal(a[2], b[2])
+        rms = np.sqrt(np.mean(np.abs(b[3].astype(np.complex128)) ** 2))
+        assert np.max(np.abs(a[3].astype(np.complex128) - b[3])) <= 2 * TOL_REL * rms
 
 
 def test_tau_extremes_all_and_none(G):
