@@ -8,10 +8,13 @@
 // this is the convolution y[n] = sum_t h[t] x[n-t] regrouped, nothing is
 // approximated.  Each G_s is a 32 x 32 complex matrix used in its real form
 // (64 x 64, as for HX), so a shift is one 128 x 64 x 64 real GEMM whose A
-// operand is the chunk array itself, started S - s rows later.  The chunk
-// array is stored once in the K-major 128-byte-swizzle layout; a start that
-// is not on an 8-row boundary is given to the tensor core through the
-// descriptor's base-offset field (the row phase of the swizzle pattern).
+// operand holds the chunks X_{m-s}.  All shifts read one chunk array in the
+// K-major 128-byte-swizzle layout, permuted so that every shift starts on an
+// 8-row (1024-byte) group: GEMM row m = 8a + b carries output chunk 16b + a,
+// and stored group g in [-S, 16) holds chunks 16b + g in its rows b < 8.
+// Shift s then reads groups -s .. 15-s: its row 8a + b is group a - s, row b,
+// i.e. chunk 16b + a - s.  The S groups below 0 repeat chunks of groups
+// 16-S .. 15 one row down (plus the halo chunks before the tile).
 //
 // Accuracy: operands split a = a_hi + a_lo into FP16 and three products
 // (hi hi, hi lo, lo hi) accumulated in FP32 in tensor memory, ~2^-22
@@ -36,7 +39,7 @@ constexpr int kTR = 32;                  // complex outputs per GEMM row
 constexpr int kTRows = 128;              // GEMM rows per tile (M)
 constexpr int kTTile = kTR * kTRows;     // 4096 outputs per tile
 constexpr int kTMaxShifts = 5;           // T <= 4 * 32 + 1
-constexpr int kTARows = 136;             // chunk array rows (128 + halo, 8-aligned)
+constexpr int kTGroups = kTRows / 8;     // 8-row groups of one GEMM operand (16)
 constexpr uint32_t kTOpBytes = 64 * 128; // one 64 x 64 FP16 operand (8 KB)
 constexpr uint32_t kTIdescN64 = (1u << 4) | (static_cast<uint32_t>(64 >> 3) << 17) |
                                 (static_cast<uint32_t>(kTRows >> 4) << 24);
@@ -50,7 +53,8 @@ __host__ inline bool tc_loop_supported(int N, int B, int T) {
 
 __host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
   const int ns = tc_shifts(T);
-  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes + 2 * kTARows * 128 + 4096;
+  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes +
+         2 * static_cast<size_t>(kTGroups + ns - 1) * 1024 + 4096;
 }
 
 // Operand elements: ns shifts x {hi, lo} x 64 x 64 for FIR, {hi, lo} x 64 x 64 for HX.
@@ -94,12 +98,6 @@ __host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const floa
   return cudaGetLastError();
 }
 
-// Descriptor for a K-major 128-byte-swizzle operand whose start may sit on
-// any 128-byte row: the base offset carries the row phase of the pattern.
-__device__ __forceinline__ uint64_t umma_desc_rows(uint32_t saddr) {
-  return umma_desc_sw128(saddr) | (static_cast<uint64_t>((saddr >> 7) & 7u) << 49);
-}
-
 struct TcLoopParams {
   LoopParams lp;
   const uint16_t *fir_ops;
@@ -132,8 +130,8 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
   unsigned char *bfir = base;
   unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
   unsigned char *ahi = bhx + 2 * kTOpBytes;
-  unsigned char *alo = ahi + kTARows * 128;
-  unsigned char *misc = alo + kTARows * 128;
+  unsigned char *alo = ahi + (kTGroups + S) * 1024;
+  unsigned char *misc = alo + (kTGroups + S) * 1024;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);               // [2]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 16);
   int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 20);
@@ -177,7 +175,8 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
 
   const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
   const int qd = warp & 3, hf = warp >> 2;
-  const int m = qd * 32 + lane;  // tile row owned in the epilogues
+  const int m = qd * 32 + lane;               // TMEM lane (GEMM row) owned in the epilogues
+  const int jc = 16 * (m & 7) + (m >> 3);     // output chunk of FIR GEMM row m
   for (;;) {
     if (tid == 0) {
       const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
@@ -203,12 +202,12 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     __syncthreads();
     if (*s_cnt < 0) break;
 
-    // ---- FIR A operand: chunk array rows j + S for chunks j in [-S, 128)
+    // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g
     const float2 *cur = f.src.frame(k);
     const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
-    for (int q = tid; q < (kTRows + S) * 8; q += 256) {
+    for (int q = tid; q < (kTGroups + S) * 64; q += 256) {
       const int row = q >> 3, pc = q & 7;
-      const int j = row - S;
+      const int j = 16 * (row & 7) + (row >> 3) - S;
       const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
       float v[8];
       if (j >= 0) {
@@ -251,7 +250,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
       tc_fence_after();
       const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), b0 = smem_u32(bfir);
       for (int s = 0; s < ns; ++s) {
-        const uint32_t arow = static_cast<uint32_t>(S - s) * 128u;
+        const uint32_t arow = static_cast<uint32_t>(S - s) * 1024u;  // group -s
         const uint32_t pa[3] = {ah + arow, ah + arow, al + arow};
         const uint32_t bh = b0 + static_cast<uint32_t>(2 * s) * kTOpBytes, bl = bh + kTOpBytes;
         const uint32_t pb[3] = {bh, bl, bh};
@@ -259,7 +258,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
         for (int pass = 0; pass < 3; ++pass)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            umma_f16(tmem, umma_desc_rows(pa[pass] + ks * 32), umma_desc_rows(pb[pass] + ks * 32), kTIdescN64,
+            umma_f16(tmem, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32), kTIdescN64,
                      (s > 0 || pass > 0 || ks > 0) ? 1u : 0u);
       }
       umma_commit(smem_u32(&mbar[0]));
@@ -273,7 +272,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     if (*s_flag) { failed = true; break; }
     tc_fence_after();
 
-    // ---- DET: FIR outputs of row m, complex columns [16 hf, 16 hf + 16)
+    // ---- DET: FIR outputs of chunk jc (GEMM row m), complex columns [16 hf, 16 hf + 16)
     float y[32];
     {
       float t16[16];
@@ -291,7 +290,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
       y[i] *= 1.f / kTScale;
       e = fmaf(y[i], y[i], e);
     }
-    eth[m * 2 + hf] = m < rows_valid ? e : 0.f;
+    eth[jc * 2 + hf] = jc < rows_valid ? e : 0.f;
     __syncthreads();
     const int rpb = f.B / kTR;  // rows per block
     const int nb = nv / f.B;
@@ -317,10 +316,10 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     __syncthreads();
     const int cnt = *s_cnt;
     // selected rows become rows of the HX A operand (the FIR operand area is free)
-    if (m < rows_valid) {
-      const int rk = s_rank[m / rpb];
+    if (jc < rows_valid) {
+      const int rk = s_rank[jc / rpb];
       if (rk >= 0) {
-        const int hrow = rk * rpb + m % rpb;
+        const int hrow = rk * rpb + jc % rpb;
 #pragma unroll
         for (int pp = 0; pp < 4; ++pp) {
           const uint32_t off = static_cast<uint32_t>(hrow) * 128u +
@@ -362,7 +361,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
         for (int pass = 0; pass < 3; ++pass)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            umma_f16(tmem + 64u, umma_desc_rows(pa[pass] + ks * 32), umma_desc_rows(pb[pass] + ks * 32), kTIdescN64,
+            umma_f16(tmem + 64u, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32), kTIdescN64,
                      (pass > 0 || ks > 0) ? 1u : 0u);
         umma_commit(smem_u32(&mbar[1]));
       }
