@@ -40,6 +40,7 @@ constexpr int kTRows = 128;              // GEMM rows per tile (M)
 constexpr int kTTile = kTR * kTRows;     // 4096 outputs per tile
 constexpr int kTMaxShifts = 5;           // T <= 4 * 32 + 1
 constexpr int kTGroups = kTRows / 8;     // 8-row groups of one GEMM operand (16)
+constexpr int kTMaxPieces = (kTGroups + kTMaxShifts - 1) * 64 / 256;  // per thread (5)
 constexpr uint32_t kTOpBytes = 64 * 128; // one 64 x 64 FP16 operand (8 KB)
 constexpr uint32_t kTIdescN64 = (1u << 4) | (static_cast<uint32_t>(64 >> 3) << 17) |
                                 (static_cast<uint32_t>(kTRows >> 4) << 24);
@@ -51,10 +52,17 @@ __host__ inline bool tc_loop_supported(int N, int B, int T) {
   return N == 32 && B % kTR == 0 && B <= kTTile && kTTile % B == 0 && T <= (kTMaxShifts - 1) * kTR + 1;
 }
 
+// Two independent tile pipelines per CTA (256 threads each) share the tap
+// and H operands; each has its own chunk array, mbarriers and 128 TMEM columns.
+constexpr int kTPipes = 2;
+constexpr int kTThreads = 256 * kTPipes;
+
+__host__ __device__ inline size_t tc_pipe_bytes(int T) {
+  return 2 * static_cast<size_t>(kTGroups + tc_shifts(T) - 1) * 1024 + 4096;
+}
 __host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
   const int ns = tc_shifts(T);
-  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes +
-         2 * static_cast<size_t>(kTGroups + ns - 1) * 1024 + 4096;
+  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes + kTPipes * tc_pipe_bytes(T);
 }
 
 // Operand elements: ns shifts x {hi, lo} x 64 x 64 for FIR, {hi, lo} x 64 x 64 for HX.
@@ -120,7 +128,7 @@ __device__ __forceinline__ uint4 split_pack8(const float *v, bool lo) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopParams tp) {
+static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcLoopParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const LoopParams &p = tp.lp;
   const FirParams &f = p.f;
@@ -129,11 +137,14 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
                                                           ~static_cast<uintptr_t>(1023));
   unsigned char *bfir = base;
   unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
-  unsigned char *ahi = bhx + 2 * kTOpBytes;
+  const int cta_tid = threadIdx.x, cta_warp = cta_tid >> 5;
+  const int pipe = cta_tid >> 8;  // tile pipeline of this thread
+  unsigned char *pipe0 = bhx + 2 * kTOpBytes;
+  unsigned char *ahi = pipe0 + pipe * tc_pipe_bytes(f.T);
   unsigned char *alo = ahi + (kTGroups + S) * 1024;
   unsigned char *misc = alo + (kTGroups + S) * 1024;
+  uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 16);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);               // [2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 16);
   int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 20);
   int32_t *s_cnt = reinterpret_cast<int32_t *>(misc + 24);
   long long *s_prefix = reinterpret_cast<long long *>(misc + 32);
@@ -141,17 +152,20 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
   int32_t *s_rank = reinterpret_cast<int32_t *>(misc + 64);          // [128] (blocks per tile <= 128)
   float *eth = reinterpret_cast<float *>(misc + 64 + 512);           // [256]
   float *Et = eth + 256;                                              // [128]
+  float *red8 = Et + 128;                                             // [8]
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = cta_tid & 255, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
+  // barrier of this pipeline's 256 threads (named barrier 1 + pipe)
+  auto psync = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(1 + pipe) : "memory"); };
 
   // constant operands, once per CTA
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(tp.fir_ops);
     uint4 *dst = reinterpret_cast<uint4 *>(bfir);
-    for (int q = tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += 256) dst[q] = src[q];
+    for (int q = cta_tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += kTThreads) dst[q] = src[q];
     const uint4 *hsrc = reinterpret_cast<const uint4 *>(tp.hx_ops);
     uint4 *hdst = reinterpret_cast<uint4 *>(bhx);
-    for (int q = tid; q < static_cast<int>(2 * kTOpBytes / 16); q += 256) hdst[q] = hsrc[q];
+    for (int q = cta_tid; q < static_cast<int>(2 * kTOpBytes / 16); q += kTThreads) hdst[q] = hsrc[q];
   }
   if (tid == 0) {
     mbar_init(smem_u32(&mbar[0]), 1);
@@ -159,9 +173,9 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *s_flag = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(128u)
+  if (cta_warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot0)),
+                 "r"(128u * kTPipes)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -169,7 +183,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tmem_slot0 + 128u * static_cast<uint32_t>(pipe);  // this pipeline's columns
   uint32_t ph0 = 0, ph1 = 0;
   bool failed = false;
 
@@ -177,12 +191,15 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
   const int qd = warp & 3, hf = warp >> 2;
   const int m = qd * 32 + lane;               // TMEM lane (GEMM row) owned in the epilogues
   const int jc = 16 * (m & 7) + (m >> 3);     // output chunk of FIR GEMM row m
+  const int npieces = (kTGroups + S) * 64;    // 16-byte pieces of the chunk array
+  uint64_t f0_seen = 0;                       // thread 0: last f0 counter value read
+  bool fir_pending = false, hx_pending = false;
   for (;;) {
     if (tid == 0) {
       const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
       *s_ticket = ld_volatile_u32(&p.ls->abort) ? ~0ull : tk;
     }
-    __syncthreads();
+    psync();
     const unsigned long long t = *s_ticket;
     if (t >= total) break;
     const int k = static_cast<int>(t / f.tiles);
@@ -192,58 +209,75 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     const int nv = static_cast<int>(min(static_cast<int64_t>(kTTile), f.L - s0));
     const int rows_valid = nv / kTR;
 
-    // firing rule of FIR on f0 (device counter, bounded wait)
+    // firing rule of FIR on f0 (device counter, bounded wait; read again only
+    // when a frame beyond the last value seen is needed)
     if (tid == 0) {
       const uint64_t need = (seq + 1) * static_cast<uint64_t>(f.F);
-      const bool ok = bounded_wait(p, [&] { return ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]) >= need; },
-                                   kActFir, 0, seq);
+      bool ok = true;
+      if (f0_seen < need)
+        ok = bounded_wait(p, [&] {
+          f0_seen = ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]);
+          return f0_seen >= need;
+        }, kActFir, 0, seq);
       *s_cnt = ok ? 0 : -1;
     }
-    __syncthreads();
+    psync();
     if (*s_cnt < 0) break;
 
-    // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g
+    // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g.
+    // All global loads of a thread are issued before any conversion.
     const float2 *cur = f.src.frame(k);
     const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
-    for (int q = tid; q < (kTGroups + S) * 64; q += 256) {
-      const int row = q >> 3, pc = q & 7;
-      const int j = 16 * (row & 7) + (row >> 3) - S;
-      const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
-      float v[8];
-      if (j >= 0) {
-        if (kTR * j + 4 * pc < nv) {
-          const float4 *src = reinterpret_cast<const float4 *>(cur + pos0);
-          const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
-          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
-          v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+    {
+      float v[kTMaxPieces][8];
+#pragma unroll
+      for (int i = 0; i < kTMaxPieces; ++i) {
+        const int q = tid + 256 * i;
+        if (q >= npieces) continue;
+        const int row = q >> 3, pc = q & 7;
+        const int j = 16 * (row & 7) + (row >> 3) - S;
+        const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
+        if (j >= 0) {
+          if (kTR * j + 4 * pc < nv) {
+            const float4 *src = reinterpret_cast<const float4 *>(cur + pos0);
+            const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
+            v[i][0] = u0.x; v[i][1] = u0.y; v[i][2] = u0.z; v[i][3] = u0.w;
+            v[i][4] = u1.x; v[i][5] = u1.y; v[i][6] = u1.z; v[i][7] = u1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[i][e] = 0.f;
+          }
         } else {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] = 0.f;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int64_t pos = pos0 + e;
-          const int64_t d = s0 - pos;
-          float2 x = make_float2(0.f, 0.f);
-          if (d <= f.T - 1) {
-            if (pos >= 0) x = cur[pos];
-            else if (prev) x = prev[f.L + pos];
-            else if (f.hist) x = f.hist[f.T - 1 + pos];
+          for (int e = 0; e < 4; ++e) {
+            const int64_t pos = pos0 + e;
+            const int64_t d = s0 - pos;
+            float2 x = make_float2(0.f, 0.f);
+            if (d <= f.T - 1) {
+              if (pos >= 0) x = cur[pos];
+              else if (prev) x = prev[f.L + pos];
+              else if (f.hist) x = f.hist[f.T - 1 + pos];
+            }
+            v[i][2 * e] = x.x;
+            v[i][2 * e + 1] = x.y;
           }
-          v[2 * e] = x.x;
-          v[2 * e + 1] = x.y;
         }
       }
-      const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-      *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v, false);
-      *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v, true);
+#pragma unroll
+      for (int i = 0; i < kTMaxPieces; ++i) {
+        const int q = tid + 256 * i;
+        if (q >= npieces) continue;
+        const int row = q >> 3, pc = q & 7;
+        const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+        *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v[i], false);
+        *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v[i], true);
+      }
     }
     if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
       for (int i = tid; i < f.T - 1; i += 256) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
+    psync();
 
     // ---- FIR GEMM: ns shifts x 3 passes x 4 K-steps of 128 x 64 x 16
     if (tid == 0) {
@@ -263,12 +297,15 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
       }
       umma_commit(smem_u32(&mbar[0]));
     }
-    if (!mbar_wait_bounded(smem_u32(&mbar[0]), ph0, p.timeout_ns)) {
+    fir_pending = true;
+    if (mbar_wait_bounded(smem_u32(&mbar[0]), ph0, p.timeout_ns)) {
+      ph0 ^= 1u;
+      fir_pending = false;
+    } else {
       if (tid == 0) report_error(p.status, kDevTimeout, kActFir, 2, seq);
       *s_flag = 1;
     }
-    ph0 ^= 1u;
-    __syncthreads();
+    psync();
     if (*s_flag) { failed = true; break; }
     tc_fence_after();
 
@@ -291,16 +328,30 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
       e = fmaf(y[i], y[i], e);
     }
     eth[jc * 2 + hf] = jc < rows_valid ? e : 0.f;
-    __syncthreads();
+    psync();
+    // block energies: eth is ordered (chunk, half); block b owns entries
+    // [2 rpb b, 2 rpb (b+1)); a shuffle tree per 32 entries in a fixed order
     const int rpb = f.B / kTR;  // rows per block
     const int nb = nv / f.B;
-    if (tid < nb) {
-      float E = 0.f;
-      for (int r = 0; r < rpb; ++r) E += eth[(tid * rpb + r) * 2] + eth[(tid * rpb + r) * 2 + 1];
-      Et[tid] = E;
-      if (f.energy) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + tid] = E;
+    {
+      const int per = 2 * rpb;  // entries per block: a power of two >= 2
+      float v = eth[tid];
+      const int seg = per < 32 ? per : 32;
+      for (int off = seg >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (per <= 32) {
+        if ((tid & (seg - 1)) == 0 && tid / per < nb) Et[tid / per] = v;
+      } else {
+        if (lane == 0) red8[warp] = v;
+      }
+      psync();
+      if (per > 32 && tid < nb) {
+        float E = 0.f;
+        for (int w = 0; w < per / 32; ++w) E += red8[tid * (per / 32) + w];
+        Et[tid] = E;
+      }
+      psync();
+      if (f.energy && tid < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + tid] = Et[tid];
     }
-    __syncthreads();
     // ---- SEL inside the tile: stable ballot compaction
     if (warp == 0) {
       int cnt = 0;
@@ -313,7 +364,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
       }
       if (lane == 0) *s_cnt = cnt;
     }
-    __syncthreads();
+    psync();
     const int cnt = *s_cnt;
     // selected rows become rows of the HX A operand (the FIR operand area is free)
     if (jc < rows_valid) {
@@ -329,15 +380,32 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
         }
       }
     }
-    // ---- SEL across tiles: decoupled look-back
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    psync();
+    // ---- HX_b GEMM on the compacted rows (needs no prefix: issued first) ...
+    if (cnt > 0) {
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), bh = smem_u32(bhx), bl = bh + kTOpBytes;
+        const uint32_t pa[3] = {ah, ah, al}, pb[3] = {bh, bl, bh};
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_f16(tmem + 64u, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32),
+                     kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
+        umma_commit(smem_u32(&mbar[1]));
+      }
+      hx_pending = true;
+    }
+    // ... while one warp runs the look-back for the tile's offset in the frame
     const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
     if (warp == 0) {
       const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
       if (lane == 0) *s_prefix = pr;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
+    psync();
     const long long prefix = *s_prefix;
     if (prefix < 0) { failed = true; break; }
     if (prefix + cnt > f.F) {
@@ -351,26 +419,16 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     const int64_t rs = p.rslot.slot(k);
     if (tid < nb && s_rank[tid] >= 0) p.rec_idx[rs * f.F + prefix + s_rank[tid]] = static_cast<int32_t>(s0 / f.B) + tid;
 
-    // ---- HX_b GEMM on the compacted rows, then the SINK payload
+    // ---- SINK payload: HX_b outputs at their compacted positions
     if (cnt > 0) {
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), bh = smem_u32(bhx), bl = bh + kTOpBytes;
-        const uint32_t pa[3] = {ah, ah, al}, pb[3] = {bh, bl, bh};
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            umma_f16(tmem + 64u, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32), kTIdescN64,
-                     (pass > 0 || ks > 0) ? 1u : 0u);
-        umma_commit(smem_u32(&mbar[1]));
-      }
-      if (!mbar_wait_bounded(smem_u32(&mbar[1]), ph1, p.timeout_ns)) {
+      if (mbar_wait_bounded(smem_u32(&mbar[1]), ph1, p.timeout_ns)) {
+        ph1 ^= 1u;
+        hx_pending = false;
+      } else {
         if (tid == 0) report_error(p.status, kDevTimeout, kActHx, 7, seq);
         *s_flag = 1;
       }
-      ph1 ^= 1u;
-      __syncthreads();
+      psync();
       if (*s_flag) { failed = true; break; }
       tc_fence_after();
       float o[32];
@@ -396,7 +454,7 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
 
     // ---- frame completion: the last tile to finish writes the SINK record
     tc_fence_before();
-    __syncthreads();
+    psync();
     if (tid == 0) {
       __threadfence();
       const uint32_t old = atomicAdd(&p.done[fslot], 1u);
@@ -413,16 +471,17 @@ static __global__ void __launch_bounds__(256, 2) firing_loop_tc_kernel(TcLoopPar
     }
   }
 
-  // leave: let MMAs in flight land (bounded) before freeing tensor memory
+  // leave: let MMAs still in flight land (bounded) before freeing tensor memory
   if (failed) {
-    mbar_wait_bounded(smem_u32(&mbar[0]), ph0 ^ 1u, p.timeout_ns);
-    mbar_wait_bounded(smem_u32(&mbar[1]), ph1 ^ 1u, p.timeout_ns);
+    if (fir_pending) mbar_wait_bounded(smem_u32(&mbar[0]), ph0, p.timeout_ns);
+    if (hx_pending) mbar_wait_bounded(smem_u32(&mbar[1]), ph1, p.timeout_ns);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (cta_warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot0), "r"(128u * kTPipes)
+                 : "memory");
   }
 }
 

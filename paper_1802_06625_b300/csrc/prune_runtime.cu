@@ -353,20 +353,25 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
     const size_t smem = tc_loop_smem_bytes(d.T);
     cudaError_t e = cudaFuncSetAttribute(firing_loop_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
+    if (e == cudaSuccess)  // two CTAs per SM need the largest shared-memory carveout
+      e = cudaFuncSetAttribute(firing_loop_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     int occ = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, firing_loop_tc_kernel, 256, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, firing_loop_tc_kernel, kTThreads, smem);
     if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop: ") + cudaGetErrorString(e));
     occ = std::max(occ, 1);
     const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
-    const int grid = static_cast<int>(std::min<unsigned long long>(ttotal, static_cast<unsigned long long>(g->sms) * occ));
+    // each CTA runs kTPipes tile pipelines
+    const unsigned long long ctas = (ttotal + kTPipes - 1) / kTPipes;
+    const int grid = static_cast<int>(std::min<unsigned long long>(ctas, static_cast<unsigned long long>(g->sms) * occ));
     {
       KTimer kt(g, 6);
-      firing_loop_tc_kernel<<<grid, 256, smem, g->stream>>>(tp);
+      firing_loop_tc_kernel<<<grid, kTThreads, smem, g->stream>>>(tp);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop launch: ") + cudaGetErrorString(e));
-    g->ticket_base += ttotal + static_cast<unsigned long long>(grid);
+    g->ticket_base += ttotal + static_cast<unsigned long long>(grid) * kTPipes;  // one failing claim per pipeline
     return PRUNE_OK;
   }
   const unsigned long long total = static_cast<unsigned long long>(n) * g->tiles;
