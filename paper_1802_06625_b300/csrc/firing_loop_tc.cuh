@@ -52,17 +52,18 @@ __host__ inline bool tc_loop_supported(int N, int B, int T) {
   return N == 32 && B % kTR == 0 && B <= kTTile && kTTile % B == 0 && T <= (kTMaxShifts - 1) * kTR + 1;
 }
 
-// Two independent tile pipelines per CTA (256 threads each) share the tap
-// and H operands; each has its own chunk array, mbarriers and 128 TMEM columns.
-constexpr int kTPipes = 2;
-constexpr int kTThreads = 256 * kTPipes;
-
+// Tile pipelines: NP independent pipelines of 128 threads per CTA share the
+// tap and H operands; each has its own chunk array, mbarriers and 128 TMEM
+// columns, so NP tiles are in flight per SM (4 when T <= 65, else 3, as far
+// as shared memory allows).
+constexpr int kTPipeThreads = 128;
+__host__ __device__ inline int tc_pipes(int T) { return tc_shifts(T) <= 3 ? 4 : 3; }
 __host__ __device__ inline size_t tc_pipe_bytes(int T) {
-  return 2 * static_cast<size_t>(kTGroups + tc_shifts(T) - 1) * 1024 + 4096;
+  return 2 * static_cast<size_t>(kTGroups + tc_shifts(T) - 1) * 1024 + 2048;
 }
 __host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
-  const int ns = tc_shifts(T);
-  return 1024 + static_cast<size_t>(ns) * 2 * kTOpBytes + 2 * kTOpBytes + kTPipes * tc_pipe_bytes(T);
+  return 1024 + static_cast<size_t>(tc_shifts(T)) * 2 * kTOpBytes + 2 * kTOpBytes +
+         static_cast<size_t>(tc_pipes(T)) * tc_pipe_bytes(T);
 }
 
 // Operand elements: ns shifts x {hi, lo} x 64 x 64 for FIR, {hi, lo} x 64 x 64 for HX.
@@ -128,7 +129,8 @@ __device__ __forceinline__ uint4 split_pack8(const float *v, bool lo) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcLoopParams tp) {
+template <int NP>
+static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_kernel(TcLoopParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const LoopParams &p = tp.lp;
   const FirParams &f = p.f;
@@ -138,34 +140,35 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
   unsigned char *bfir = base;
   unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
   const int cta_tid = threadIdx.x, cta_warp = cta_tid >> 5;
-  const int pipe = cta_tid >> 8;  // tile pipeline of this thread
+  const int pipe = cta_tid / kTPipeThreads;
   unsigned char *pipe0 = bhx + 2 * kTOpBytes;
-  unsigned char *ahi = pipe0 + pipe * tc_pipe_bytes(f.T);
+  const size_t pbytes = tc_pipe_bytes(f.T);
+  unsigned char *ahi = pipe0 + pipe * pbytes;
   unsigned char *alo = ahi + (kTGroups + S) * 1024;
   unsigned char *misc = alo + (kTGroups + S) * 1024;
-  uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 16);
   uint64_t *mbar = reinterpret_cast<uint64_t *>(misc);               // [2]
-  int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 20);
-  int32_t *s_cnt = reinterpret_cast<int32_t *>(misc + 24);
-  long long *s_prefix = reinterpret_cast<long long *>(misc + 32);
-  unsigned long long *s_ticket = reinterpret_cast<unsigned long long *>(misc + 40);
-  int32_t *s_rank = reinterpret_cast<int32_t *>(misc + 64);          // [128] (blocks per tile <= 128)
-  float *eth = reinterpret_cast<float *>(misc + 64 + 512);           // [256]
-  float *Et = eth + 256;                                              // [128]
-  float *red8 = Et + 128;                                             // [8]
+  int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 16);
+  int32_t *s_cnt = reinterpret_cast<int32_t *>(misc + 20);
+  unsigned long long *s_ticket = reinterpret_cast<unsigned long long *>(misc + 24);
+  long long *s_prefix = reinterpret_cast<long long *>(misc + 40);
+  int32_t *s_rank = reinterpret_cast<int32_t *>(misc + 64);          // [128] blocks of a tile
+  float *eth = reinterpret_cast<float *>(misc + 576);                 // [128] chunk energies
+  float *Et = eth + 128;                                              // [128] block energies
+  float *red4 = Et + 128;                                             // [4]
+  uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 32);
 
-  const int tid = cta_tid & 255, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
-  // barrier of this pipeline's 256 threads (named barrier 1 + pipe)
-  auto psync = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(1 + pipe) : "memory"); };
+  const int tid = cta_tid % kTPipeThreads, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
+  // barrier of this pipeline's 128 threads (named barrier 1 + pipe)
+  auto psync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + pipe) : "memory"); };
 
   // constant operands, once per CTA
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(tp.fir_ops);
     uint4 *dst = reinterpret_cast<uint4 *>(bfir);
-    for (int q = cta_tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += kTThreads) dst[q] = src[q];
+    for (int q = cta_tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += NP * kTPipeThreads) dst[q] = src[q];
     const uint4 *hsrc = reinterpret_cast<const uint4 *>(tp.hx_ops);
     uint4 *hdst = reinterpret_cast<uint4 *>(bhx);
-    for (int q = cta_tid; q < static_cast<int>(2 * kTOpBytes / 16); q += kTThreads) hdst[q] = hsrc[q];
+    for (int q = cta_tid; q < static_cast<int>(2 * kTOpBytes / 16); q += NP * kTPipeThreads) hdst[q] = hsrc[q];
   }
   if (tid == 0) {
     mbar_init(smem_u32(&mbar[0]), 1);
@@ -175,7 +178,7 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
   }
   if (cta_warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot0)),
-                 "r"(128u * kTPipes)
+                 "r"(512u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -184,15 +187,16 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot0 + 128u * static_cast<uint32_t>(pipe);  // this pipeline's columns
+  // TMEM lanes of warp `warp` (the CTA warp index mod 4 equals it)
+  const uint32_t tlane = static_cast<uint32_t>(warp * 32) << 16;
   uint32_t ph0 = 0, ph1 = 0;
   bool failed = false;
 
   const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
-  const int qd = warp & 3, hf = warp >> 2;
-  const int m = qd * 32 + lane;               // TMEM lane (GEMM row) owned in the epilogues
-  const int jc = 16 * (m & 7) + (m >> 3);     // output chunk of FIR GEMM row m
-  const int npieces = (kTGroups + S) * 64;    // 16-byte pieces of the chunk array
-  uint64_t f0_seen = 0;                       // thread 0: last f0 counter value read
+  const int m = tid;                           // TMEM lane (GEMM row) owned by this thread
+  const int jc = 16 * (m & 7) + (m >> 3);      // output chunk of FIR GEMM row m
+  const int npieces = (kTGroups + S) * 64;     // 16-byte pieces of the chunk array
+  uint64_t f0_seen = 0;                        // thread 0: last f0 counter value read
   bool fir_pending = false, hx_pending = false;
   for (;;) {
     if (tid == 0) {
@@ -225,14 +229,14 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
     if (*s_cnt < 0) break;
 
     // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g.
-    // All global loads of a thread are issued before any conversion.
+    // A thread's global loads are issued in batches before conversion.
     const float2 *cur = f.src.frame(k);
     const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
-    {
+    for (int q0 = 0; q0 < npieces; q0 += kTMaxPieces * kTPipeThreads) {
       float v[kTMaxPieces][8];
 #pragma unroll
       for (int i = 0; i < kTMaxPieces; ++i) {
-        const int q = tid + 256 * i;
+        const int q = q0 + tid + kTPipeThreads * i;
         if (q >= npieces) continue;
         const int row = q >> 3, pc = q & 7;
         const int j = 16 * (row & 7) + (row >> 3) - S;
@@ -265,7 +269,7 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
       }
 #pragma unroll
       for (int i = 0; i < kTMaxPieces; ++i) {
-        const int q = tid + 256 * i;
+        const int q = q0 + tid + kTPipeThreads * i;
         if (q >= npieces) continue;
         const int row = q >> 3, pc = q & 7;
         const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
@@ -274,7 +278,7 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
       }
     }
     if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
-      for (int i = tid; i < f.T - 1; i += 256) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
+      for (int i = tid; i < f.T - 1; i += kTPipeThreads) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     psync();
@@ -309,44 +313,37 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
     if (*s_flag) { failed = true; break; }
     tc_fence_after();
 
-    // ---- DET: FIR outputs of chunk jc (GEMM row m), complex columns [16 hf, 16 hf + 16)
-    float y[32];
+    // ---- DET: energy of chunk jc (GEMM row m), both column halves
     {
-      float t16[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(hf * 32), t16);
+      float e = 0.f;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) y[e] = t16[e];
-      tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(hf * 32 + 16), t16);
+      for (int h = 0; h < 4; ++h) {
+        float t16[16];
+        tmem_ld16(tmem + tlane + static_cast<uint32_t>(h * 16), t16);
+        tmem_ld_wait();
 #pragma unroll
-      for (int e = 0; e < 16; ++e) y[16 + e] = t16[e];
-      tmem_ld_wait();
+        for (int i = 0; i < 16; ++i) e = fmaf(t16[i], t16[i], e);
+      }
+      eth[jc] = jc < rows_valid ? e * (1.f / (kTScale * kTScale)) : 0.f;
     }
-    float e = 0.f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      y[i] *= 1.f / kTScale;
-      e = fmaf(y[i], y[i], e);
-    }
-    eth[jc * 2 + hf] = jc < rows_valid ? e : 0.f;
     psync();
-    // block energies: eth is ordered (chunk, half); block b owns entries
-    // [2 rpb b, 2 rpb (b+1)); a shuffle tree per 32 entries in a fixed order
-    const int rpb = f.B / kTR;  // rows per block
+    // block energies: eth is ordered by chunk; block b owns [rpb b, rpb (b+1));
+    // a shuffle tree per segment of the warp, in a fixed order
+    const int rpb = f.B / kTR;  // rows (chunks) per block
     const int nb = nv / f.B;
     {
-      const int per = 2 * rpb;  // entries per block: a power of two >= 2
       float v = eth[tid];
-      const int seg = per < 32 ? per : 32;
+      const int seg = rpb < 32 ? rpb : 32;
       for (int off = seg >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (per <= 32) {
-        if ((tid & (seg - 1)) == 0 && tid / per < nb) Et[tid / per] = v;
+      if (rpb <= 32) {
+        if ((tid & (seg - 1)) == 0 && tid / rpb < nb) Et[tid / rpb] = v;
       } else {
-        if (lane == 0) red8[warp] = v;
+        if (lane == 0) red4[warp] = v;
       }
       psync();
-      if (per > 32 && tid < nb) {
+      if (rpb > 32 && tid < nb) {
         float E = 0.f;
-        for (int w = 0; w < per / 32; ++w) E += red8[tid * (per / 32) + w];
+        for (int w = 0; w < rpb / 32; ++w) E += red4[tid * (rpb / 32) + w];
         Et[tid] = E;
       }
       psync();
@@ -366,17 +363,32 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
     }
     psync();
     const int cnt = *s_cnt;
-    // selected rows become rows of the HX A operand (the FIR operand area is free)
-    if (jc < rows_valid) {
-      const int rk = s_rank[jc / rpb];
-      if (rk >= 0) {
-        const int hrow = rk * rpb + jc % rpb;
+    // selected rows become rows of the HX A operand (the FIR operand area is
+    // free): the FIR accumulators are read a second time, half a row at a time
+    {
+      const int rk = jc < rows_valid ? s_rank[jc / rpb] : -1;
+      const int hrow = rk * rpb + jc % rpb;
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) {
-          const uint32_t off = static_cast<uint32_t>(hrow) * 128u +
-                               (static_cast<uint32_t>((4 * hf + pp) ^ (hrow & 7)) << 4);
-          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(y + 8 * pp, false);
-          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(y + 8 * pp, true);
+      for (int hf = 0; hf < 2; ++hf) {
+        float y[32];
+        {
+          float t16[16];
+          tmem_ld16(tmem + tlane + static_cast<uint32_t>(hf * 32), t16);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[i] = t16[i] * (1.f / kTScale);
+          tmem_ld16(tmem + tlane + static_cast<uint32_t>(hf * 32 + 16), t16);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) y[16 + i] = t16[i] * (1.f / kTScale);
+          tmem_ld_wait();
+        }
+        if (rk >= 0) {
+#pragma unroll
+          for (int pp = 0; pp < 4; ++pp) {
+            const uint32_t off = static_cast<uint32_t>(hrow) * 128u +
+                                 (static_cast<uint32_t>((4 * hf + pp) ^ (hrow & 7)) << 4);
+            *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(y + 8 * pp, false);
+            *reinterpret_cast<uint4 *>(alo + off) = split_pack8(y + 8 * pp, true);
+          }
         }
       }
     }
@@ -431,24 +443,27 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
       psync();
       if (*s_flag) { failed = true; break; }
       tc_fence_after();
-      float o[32];
-      {
-        float t16[16];
-        tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + 64u + static_cast<uint32_t>(hf * 32), t16);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) o[i] = t16[i];
-        tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + 64u + static_cast<uint32_t>(hf * 32 + 16), t16);
+      for (int hf = 0; hf < 2; ++hf) {
+        float o[32];
+        {
+          float t16[16];
+          tmem_ld16(tmem + tlane + 64u + static_cast<uint32_t>(hf * 32), t16);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) o[16 + i] = t16[i];
-        tmem_ld_wait();
-      }
-      if (m < cnt * rpb) {
-        float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
-                                                 (m % rpb) * kTR + hf * 16);
-        const float sc = 1.f / kTScale;
+          for (int i = 0; i < 16; ++i) o[i] = t16[i];
+          tmem_ld16(tmem + tlane + 64u + static_cast<uint32_t>(hf * 32 + 16), t16);
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          dst[i] = make_float4(o[4 * i] * sc, o[4 * i + 1] * sc, o[4 * i + 2] * sc, o[4 * i + 3] * sc);
+          for (int i = 0; i < 16; ++i) o[16 + i] = t16[i];
+          tmem_ld_wait();
+        }
+        if (m < cnt * rpb) {
+          float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
+                                                   (m % rpb) * kTR + hf * 16);
+          const float sc = 1.f / kTScale;
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            dst[i] = make_float4(o[4 * i] * sc, o[4 * i + 1] * sc, o[4 * i + 2] * sc, o[4 * i + 3] * sc);
+        }
       }
     }
 
@@ -480,8 +495,7 @@ static __global__ void __launch_bounds__(kTThreads, 1) firing_loop_tc_kernel(TcL
   __syncthreads();
   if (cta_warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot0), "r"(128u * kTPipes)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot0), "r"(512u) : "memory");
   }
 }
 

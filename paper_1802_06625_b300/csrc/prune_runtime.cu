@@ -298,6 +298,15 @@ static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
   return PRUNE_OK;
 }
 
+template <int NP>
+static cudaError_t launch_tc_loop(const TcLoopParams &tp, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(firing_loop_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  firing_loop_tc_kernel<NP><<<grid, NP * kTPipeThreads, smem, s>>>(tp);
+  return cudaGetLastError();
+}
+
 template <int NT>
 static cudaError_t launch_loop_nt(const LoopParams &lp, int sms, size_t smem, cudaStream_t s, int *grid_out,
                                   unsigned long long total) {
@@ -351,27 +360,18 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
     tp.hx_ops = g->tc_hx_ops;
     tp.ns = tc_shifts(d.T);
     const size_t smem = tc_loop_smem_bytes(d.T);
-    cudaError_t e = cudaFuncSetAttribute(firing_loop_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e == cudaSuccess)  // two CTAs per SM need the largest shared-memory carveout
-      e = cudaFuncSetAttribute(firing_loop_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-    int occ = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, firing_loop_tc_kernel, kTThreads, smem);
-    if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop: ") + cudaGetErrorString(e));
-    occ = std::max(occ, 1);
+    const int np = tc_pipes(d.T);
     const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
-    // each CTA runs kTPipes tile pipelines
-    const unsigned long long ctas = (ttotal + kTPipes - 1) / kTPipes;
-    const int grid = static_cast<int>(std::min<unsigned long long>(ctas, static_cast<unsigned long long>(g->sms) * occ));
+    // one CTA per SM, np tile pipelines in each
+    const int grid = static_cast<int>(std::max<unsigned long long>(
+        1, std::min<unsigned long long>((ttotal + np - 1) / np, static_cast<unsigned long long>(g->sms))));
+    cudaError_t e;
     {
       KTimer kt(g, 6);
-      firing_loop_tc_kernel<<<grid, kTThreads, smem, g->stream>>>(tp);
+      e = np == 4 ? launch_tc_loop<4>(tp, grid, smem, g->stream) : launch_tc_loop<3>(tp, grid, smem, g->stream);
     }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop launch: ") + cudaGetErrorString(e));
-    g->ticket_base += ttotal + static_cast<unsigned long long>(grid) * kTPipes;  // one failing claim per pipeline
+    g->ticket_base += ttotal + static_cast<unsigned long long>(grid) * np;  // one failing claim per pipeline
     return PRUNE_OK;
   }
   const unsigned long long total = static_cast<unsigned long long>(n) * g->tiles;
