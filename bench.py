@@ -299,8 +299,12 @@ def run_ours(args, w):
             "kernel_ms_per_step": {KIND_NAMES[k]: t / args.steps for k, (t, n) in times.items() if n},
             "clocks": clk.summary()}
 
-    # end to end through the public API: host frames in, host records out
+    # the batched form: one frame of each of 512 uneven instances per step
     del g
+    if not args.no_batched and ws == 1:
+        line["batched"] = run_batched(args, dev)
+
+    # end to end through the public API: host frames in, host records out
     line["e2e"] = run_e2e(args, w, dev, stream, rank, ws)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -311,6 +315,60 @@ def run_ours(args, w):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args, dev):
+    """Batched (one launch sequence for all instances, replayed as a CUDA
+    graph) against plain (one graph object per instance, fired one by one),
+    same frames, wall clock over K steps with the device synchronized."""
+    from paper_1802_06625_b300 import _lib
+    from paper_1802_06625_b300.graph import Batch, Graph
+
+    b = synth.BATCHED
+    ws_ = [b.instance(i) for i in range(b.instances)]
+    x = torch.cat([w.frame(0, device=dev).reshape(-1) for w in ws_])
+    insts = [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws_]
+    samples = x.numel()
+    stream = torch.cuda.Stream(device=dev)
+    bt = Batch(b.B, b.N, insts, stream=stream, device=dev.index)
+    for _ in range(args.warmup):
+        bt.fire(x, graph=True)
+    bt.sync()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bt.fire(x, graph=True)
+    bt.sync()
+    t_batched = (time.perf_counter() - t0) / args.steps
+    bt.close()
+
+    graphs = [Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=1, out_frames=1, device=dev.index) for w in ws_]
+    offs, o = [], 0
+    for w in ws_:
+        offs.append(o)
+        o += w.F * w.B
+
+    def plain_step():
+        for g, w, off in zip(graphs, ws_, offs):
+            g.push(x[off:off + w.F * w.B].view(1, w.F, w.B), mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+            g.run()
+            g.discard()
+
+    for _ in range(args.warmup):
+        plain_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plain_step()
+    torch.cuda.synchronize(dev)
+    t_plain = (time.perf_counter() - t0) / args.steps
+    for g in graphs:
+        g.close()
+    return {"workload": b.name, "instances": b.instances, "samples_per_step": samples,
+            "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
+            "plain_Msamples_s": samples / t_plain / 1e6, "plain_ms_per_step": 1e3 * t_plain,
+            "speedup": t_plain / t_batched,
+            "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
+                      "graph, plain = one graph object per instance (push, run, drop per step)"}
 
 
 def run_e2e(args, w, dev, stream, rank, ws):
@@ -370,7 +428,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default: the workload's)")
-    ap.add_argument("--C", type=int, default=3, help="buffering constant of eq. (2)")
+    ap.add_argument("--C", type=int, default=48,
+                    help="buffering constant of eq. (2): frames f0 holds, hence frames one launch can fire")
     ap.add_argument("--path", default="fused", choices=["fused", "cuda_cores", "actors"],
                     help="fused loop (tensor cores where the shape allows), fused loop on CUDA cores, "
                          "or one kernel per actor")
@@ -378,6 +437,7 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=8)
     ap.add_argument("--ref-frames", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the top kernel")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -257,6 +257,46 @@ PRUNE_API prune_status prune_hx(const void *y, const int32_t *idx, const int32_t
                       int32_t N, int32_t frames, const void *H, void *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batched firing: many independent graph instances (Sec. V: the DPGs of
+ * different instances are independent) with uneven F, T, tau, taps and H and
+ * a common B and N.  One step fires one frame of every instance: FIR with the
+ * instance's own delay token, DET, SEL, HX_b and SINK, in three launches over
+ * the whole batch (HX_b on tcgen05 when N = 64, else CUDA cores), optionally
+ * replayed as a captured CUDA graph.  Results stay on the device until pulled.
+ * ---------------------------------------------------------------------- */
+
+typedef struct prune_batch prune_batch;
+
+enum { PRUNE_BATCH_GRAPH = 1 /* prune_batch_fire: capture the step once per (x, delay-token
+                                parity) and replay it as a CUDA graph */ };
+
+/* Create a batch of n instances from n descriptors (B and N equal in all;
+ * stream, device and buffering of descs[0] apply to the batch).  The graph
+ * shape rules of prune_graph_desc hold per instance; N >= 64 must be 64. */
+PRUNE_API prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_batch **out);
+PRUNE_API prune_status prune_batch_destroy(prune_batch *b);
+
+/* Offset (in complex samples) of instance i's frame in a step's input, and
+ * the total samples of one step (the sum of F_i * B). */
+PRUNE_API prune_status prune_batch_offset(prune_batch *b, int32_t i, int64_t *offset, int64_t *total);
+
+/* Fire one frame of every instance.  x: device, complex64, 16-byte aligned,
+ * all instances' frames back to back at the offsets above; referenced until
+ * the step completes (stream order).  flags: PRUNE_BATCH_GRAPH.  Asynchronous. */
+PRUNE_API prune_status prune_batch_fire(prune_batch *b, const void *x, int32_t flags);
+
+/* Wait for the batch's work; report device errors. */
+PRUNE_API prune_status prune_batch_sync(prune_batch *b);
+
+/* Copy the last step's record of instance i (frame = step number, c, idx,
+ * compacted y) to host (PRUNE_MEM_HOST) or device (PRUNE_MEM_DEVICE) buffers.
+ * Waits for the batch. */
+PRUNE_API prune_status prune_batch_pull(prune_batch *b, int32_t i, prune_frame_out *out, int32_t mem);
+
+/* Message of the last failure on b. */
+PRUNE_API const char *prune_batch_last_error(const prune_batch *b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free firing.  The paper has no counterpart: this entry point
  * exists for callers of the library that cannot allocate device memory.
  * ---------------------------------------------------------------------- */

@@ -25,7 +25,9 @@ PRUNE_NUM_FIFOS = 8
 EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "prune_push_frames",
            "prune_run", "prune_sync", "prune_pull", "prune_peek", "prune_fifo_stats",
            "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx",
-           "prune_fire_frames_noalloc")
+           "prune_fire_frames_noalloc", "prune_batch_create", "prune_batch_destroy", "prune_batch_offset",
+           "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error")
+PRUNE_BATCH_GRAPH = 1
 
 
 class prune_graph_desc(ctypes.Structure):
@@ -75,12 +77,22 @@ def load(path: str | None = None):
         "prune_hx": [P, P, P, I32, I32, I32, I32, P, P, P],
         "prune_fire_frames_noalloc": [P, P, P, P, I32, I32, I32, I32, I32, ctypes.c_float, P, P, P, P, P, P],
     }
+    sig.update({
+        "prune_batch_create": [ctypes.POINTER(prune_graph_desc), I32, ctypes.POINTER(P)],
+        "prune_batch_destroy": [P],
+        "prune_batch_offset": [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "prune_batch_fire": [P, P, I32],
+        "prune_batch_sync": [P],
+        "prune_batch_pull": [P, I32, ctypes.POINTER(prune_frame_out), I32],
+    })
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
     lib.prune_last_error.argtypes = [P]
     lib.prune_last_error.restype = ctypes.c_char_p
+    lib.prune_batch_last_error.argtypes = [P]
+    lib.prune_batch_last_error.restype = ctypes.c_char_p
     return lib
 
 
@@ -94,8 +106,11 @@ def lib():
     return _LIB
 
 
-def check(status: int, g=None):
+def check(status: int, g=None, batch=None):
     if status != PRUNE_OK:
-        msg = lib().prune_last_error(g).decode(errors="replace")
+        if batch is not None:
+            msg = lib().prune_batch_last_error(batch).decode(errors="replace")
+        else:
+            msg = lib().prune_last_error(g).decode(errors="replace")
         raise PruneError(status, msg)
     return status

@@ -180,3 +180,64 @@ def hx(y, idx, c, H, F, B, N, stream=None):
     check(_lib.lib().prune_hx(y.data_ptr(), idx.contiguous().data_ptr(), c.contiguous().data_ptr(), F, B, N,
                               frames, H.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+class Batch:
+    """Many independent graph instances fired one frame each per step.
+    ``instances``: list of dicts with F, T, tau, taps, H (common B, N)."""
+
+    def __init__(self, B, N, instances, stream=None, device=None):
+        self.B, self.N, self.n = B, N, len(instances)
+        if device is None:
+            device = torch.cuda.current_device()
+        self._keep = []
+        descs = (_lib.prune_graph_desc * self.n)()
+        for i, inst in enumerate(instances):
+            taps = _c64_floats(inst["taps"]).reshape(-1)
+            H = _c64_floats(inst["H"]).reshape(-1)
+            self._keep += [taps, H]
+            descs[i] = _lib.prune_graph_desc(F=inst["F"], B=B, T=inst["T"], N=N, C=1, out_frames=1,
+                                             tau=float(inst["tau"]), taps=taps.ctypes.data, H=H.ctypes.data,
+                                             stream=stream.cuda_stream if (stream is not None and i == 0) else None,
+                                             device=device, reserved=0, hbm_budget=0)
+        h = ctypes.c_void_p()
+        check(_lib.lib().prune_batch_create(descs, self.n, ctypes.byref(h)))
+        self.h = h
+        self.F = [inst["F"] for inst in instances]
+        off, tot = ctypes.c_int64(), ctypes.c_int64()
+        self.offsets = []
+        for i in range(self.n):
+            check(_lib.lib().prune_batch_offset(self.h, i, ctypes.byref(off), ctypes.byref(tot)), batch=self.h)
+            self.offsets.append(off.value)
+        self.total = tot.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().prune_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fire(self, x, graph=False):
+        """x: CUDA complex64 tensor of self.total samples (instances back to back)."""
+        assert x.is_cuda and x.numel() == self.total
+        self._x = x
+        check(_lib.lib().prune_batch_fire(self.h, x.data_ptr(), _lib.PRUNE_BATCH_GRAPH if graph else 0),
+              batch=self.h)
+
+    def sync(self):
+        check(_lib.lib().prune_batch_sync(self.h), batch=self.h)
+
+    def pull(self, i):
+        F = self.F[i]
+        idx = np.zeros(F, np.int32)
+        y = np.zeros((F, self.B), np.complex64)
+        rec = _lib.prune_frame_out()
+        rec.idx = idx.ctypes.data
+        rec.y = y.ctypes.data
+        check(_lib.lib().prune_batch_pull(self.h, i, ctypes.byref(rec), _lib.PRUNE_MEM_HOST), batch=self.h)
+        return rec.frame, rec.c, idx[:rec.c].copy(), y[:rec.c].copy()

@@ -1,0 +1,101 @@
+"""Batched firing of many independent instances against the oracle: uneven
+F, T and tau, the delay token carried across steps, HX on tensor cores
+(N = 64) and on CUDA cores (N = 16), and CUDA-graph replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity import TOL_REL, compare_frame
+from paper_1802_06625_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1802_06625_b300 import graph
+    return graph
+
+
+def _instances(B, N, seed, n):
+    specs = [(16, 8), (37, 32), (5, 128), (64, 1), (130, 32), (3, 8), (200, 128), (1, 32), (90, 17), (12, 64)]
+    out = []
+    for i in range(n):
+        F, T = specs[i % len(specs)]
+        w = synth.PlainWorkload(f"b{i}", F=F, B=B, T=T, N=N, frames=3, tau=float((2 + i % 6) * B),
+                                seed=seed * 1000 + i, p=0.1 + 0.08 * (i % 10))
+        out.append(w)
+    return out
+
+
+def _run(G, B, N, ws, steps, graph):
+    insts = [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws]
+    bt = G.Batch(B, N, insts)
+    frames = [[w.frame(k) for w in ws] for k in range(steps)]
+    recs = []
+    for k in range(steps):
+        x = torch.cat([f.reshape(-1) for f in frames[k]]).cuda()
+        bt.fire(x, graph=graph)
+        bt.sync()
+        recs.append([bt.pull(i) for i in range(len(ws))])
+    bt.close()
+    return frames, recs
+
+
+@pytest.mark.parametrize("N", [64, 16])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_matches_oracle_over_steps(G, N, graph):
+    B = 256
+    ws = _instances(B, N, seed=5 + N, n=10)
+    steps = 3
+    frames, recs = _run(G, B, N, ws, steps, graph)
+    for i, w in enumerate(ws):
+        x = np.stack([frames[k][i].numpy() for k in range(steps)])
+        r = oracle.run(w.F, B, w.T, N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), x)
+        for k in range(steps):
+            frame, c, idx, y = recs[k][i]
+            assert frame == k
+            err, rms, nb = compare_frame(c, idx, y, r.c[k], r.idx[k], r.y[k], r.energy[k], np.float32(w.tau), B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (i, k, err / rms)
+
+
+def test_batch_equals_single_graphs(G):
+    B, N = 256, 64
+    ws = _instances(B, N, seed=99, n=6)
+    frames, recs = _run(G, B, N, ws, 2, graph=True)
+    for i, w in enumerate(ws):
+        g = G.Graph(w.F, B, w.T, N, w.tau, w.taps(), w.H(), C=3, out_frames=2)
+        g.push(torch.stack([frames[k][i] for k in range(2)]).cuda())
+        g.run(actors=True)
+        single = g.pull()
+        g.close()
+        for k in range(2):
+            assert single[k][1] == recs[k][i][1]
+            assert np.array_equal(single[k][2], recs[k][i][2])
+            assert np.array_equal(single[k][3], recs[k][i][3])   # same kernels arithmetic: bit-identical
+
+
+def test_batched_workload_shapes_fire(G):
+    # the 512-instance workload's shapes, one step, control checked against
+    # the oracle on a sample of instances
+    b = synth.BATCHED
+    ws = [b.instance(i) for i in range(b.instances)]
+    insts = [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws]
+    bt = G.Batch(b.B, b.N, insts)
+    x_host = torch.cat([w.frame(0).reshape(-1) for w in ws])   # generated on the CPU
+    x = x_host.cuda()
+    bt.fire(x, graph=True)
+    bt.sync()
+    for i in (0, 1, 100, 257, 511):
+        w = ws[i]
+        frame, c, idx, y = bt.pull(i)
+        xi = x_host[bt.offsets[i]:bt.offsets[i] + w.F * w.B].numpy().reshape(1, w.F, w.B)
+        r = oracle.run(w.F, w.B, w.T, w.N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), xi)
+        err, rms, nb = compare_frame(c, idx, y, r.c[0], r.idx[0], r.y[0], r.energy[0], np.float32(w.tau), w.B)
+        if rms > 0:
+            assert err <= TOL_REL * rms
+    bt.close()
