@@ -297,6 +297,36 @@ PRUNE_API prune_status prune_batch_pull(prune_batch *b, int32_t i, prune_frame_o
 PRUNE_API const char *prune_batch_last_error(const prune_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Adjoints over a recorded control trace (training the taps and H).  The
+ * decisions v[b] = E_b > tau are piecewise constant in the parameters, so
+ * with the trace (c, idx) of a forward firing held fixed the sink output is
+ * linear in H (HX_b, Sec. V) and in the taps (FIR); the blocks of inactive
+ * DCs (itr = 0) carry no gradient.  Gradients of a real loss are complex,
+ * g = dL/dRe + i dL/dIm.  Both kernels ACCUMULATE into gH / gtaps (atomic
+ * FP32 adds; the caller zeroes them); failures of argument checks return
+ * PRUNE_EINVAL with the message in prune_last_error(NULL), enqueueing nothing.
+ * ---------------------------------------------------------------------- */
+
+/* HX_b adjoint.  For every frame k and selected slot j < c[k], block
+ * b = idx[k][j], row r of B/N:  z = H w with w = y[k][b*B + r*N ...]:
+ *   gH += g_z w^H  (g_z = gout[k][j*B + r*N ...], the compacted layout of
+ *                   prune_hx's output)
+ *   gy[k][b*B + r*N ...] = H^H g_z  (written; other blocks of gy untouched)
+ *   y, gout, gy device [frames][F*B] complex64; idx, c device as from
+ *   prune_det_sel; H, gH device [N][N] complex64.  N <= 64, N divides B. */
+PRUNE_API prune_status prune_hx_adjoint(const void *y, const int32_t *idx, const int32_t *c, int32_t F,
+                                        int32_t B, int32_t N, int32_t frames, const void *H,
+                                        const void *gout, void *gy, void *gH, void *stream);
+
+/* FIR adjoint: gtaps[t] += sum_n gy[n] conj(x[n - t]) over the frames as one
+ * stream, x[n] for n < 0 taken from hist (T-1 samples, NULL = zeros).  Tiles
+ * whose gy is all zero (no selected block) exit after staging.
+ *   x, gy device [frames][F*B] complex64, 16-byte aligned; gtaps device [T].
+ * Sizes as in prune_graph_desc. */
+PRUNE_API prune_status prune_fir_adjoint(const void *x, const void *hist, const void *gy, int32_t F,
+                                         int32_t B, int32_t T, int32_t frames, void *gtaps, void *stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free firing.  The paper has no counterpart: this entry point
  * exists for callers of the library that cannot allocate device memory.
  * ---------------------------------------------------------------------- */

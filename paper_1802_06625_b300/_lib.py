@@ -26,7 +26,8 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_run", "prune_sync", "prune_pull", "prune_peek", "prune_fifo_stats",
            "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx",
            "prune_fire_frames_noalloc", "prune_batch_create", "prune_batch_destroy", "prune_batch_offset",
-           "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error")
+           "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error",
+           "prune_hx_adjoint", "prune_fir_adjoint")
 PRUNE_BATCH_GRAPH = 1
 
 
@@ -84,6 +85,8 @@ def load(path: str | None = None):
         "prune_batch_fire": [P, P, I32],
         "prune_batch_sync": [P],
         "prune_batch_pull": [P, I32, ctypes.POINTER(prune_frame_out), I32],
+        "prune_hx_adjoint": [P, P, P, I32, I32, I32, I32, P, P, P, P, P],
+        "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
     })
     for name, args in sig.items():
         f = getattr(lib, name)

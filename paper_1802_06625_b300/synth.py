@@ -171,6 +171,13 @@ PLAIN_SMALL = PlainWorkload("plain_F64_B256_T16_N16_100fr", F=64, B=256, T=16, N
 PLAIN_LARGE = PlainWorkload("plain_F4096_B1024_T64_N32_1000fr", F=4096, B=1024, T=64, N=32,
                             frames=1000, tau=4.0 * 1024, seed=2, p=None, p_lo=0.1, p_hi=0.9)
 
+# Differentiation: the 100-frame plain shapes with 64 taps and H 32x32; the
+# L2 loss is taken against the sink output of a target graph with the same
+# frames and the parameters of seed 5 (DIFF_TARGET).
+DIFF = PlainWorkload("diff_F64_B256_T64_N32_100fr", F=64, B=256, T=64, N=32, frames=100,
+                     tau=4.0 * 256, seed=4, p=0.25)
+DIFF_TARGET_SEED = 5
+
 
 @dataclass
 class BatchedWorkload:
