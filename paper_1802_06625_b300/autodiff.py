@@ -98,12 +98,14 @@ def fire(taps, H, x, hist=None, *, F, B, T, N, tau, store=True):
 
 def scatter(out, c, idx, F, B):
     """Compacted sink output -> [frames, F, B] with the selected blocks at
-    their places and zeros elsewhere (torch indexing, differentiable)."""
+    their places and zeros elsewhere (torch indexing, differentiable; the
+    graph exists even when no block is selected)."""
     frames = out.shape[0]
-    scat = torch.zeros(frames, F, B, dtype=out.dtype, device=out.device)
-    cc = c.tolist()
-    for k in range(frames):
-        if cc[k]:
-            sel = idx[k, :cc[k]].long()
-            scat[k, sel] = out[k, :cc[k] * B].view(cc[k], B)
-    return scat
+    j = torch.arange(F, device=out.device)
+    sel = j[None, :] < c[:, None].long()                       # slot j of frame k holds a block
+    k, jj = sel.nonzero(as_tuple=True)
+    src = k * F + jj
+    dst = k * F + idx[k, jj].long()
+    rows = out.reshape(frames * F, B)[src]
+    scat = torch.zeros(frames * F, B, dtype=out.dtype, device=out.device).index_copy(0, dst, rows)
+    return scat.view(frames, F, B)

@@ -57,7 +57,7 @@ def _gpu_grad(AD, w, x, taps, H, hist, target, store):
     loss = (d.real.square() + d.imag.square()).sum()
     loss.backward()
     torch.cuda.synchronize()
-    return float(loss), t.grad.cpu().numpy(), h.grad.cpu().numpy(), c.cpu().numpy(), idx.cpu().numpy()
+    return float(loss.detach()), t.grad.cpu().numpy(), h.grad.cpu().numpy(), c.cpu().numpy(), idx.cpu().numpy()
 
 
 def _rel(a, b):
