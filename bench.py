@@ -304,6 +304,10 @@ def run_ours(args, w):
     if not args.no_batched and ws == 1:
         line["batched"] = run_batched(args, dev)
 
+    # the request loop: Poisson stream arrivals, admission by HBM budget
+    if not args.no_serving and ws == 1:
+        line["serving"] = run_serving(args, dev)
+
     # end to end through the public API: host frames in, host records out
     line["e2e"] = run_e2e(args, w, dev, stream, rank, ws)
 
@@ -369,6 +373,85 @@ def run_batched(args, dev):
             "speedup": t_plain / t_batched,
             "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
                       "graph, plain = one graph object per instance (push, run, drop per step)"}
+
+
+def run_serving(args, dev):
+    """Streams arrive on the host clock as a Poisson process; each is admitted
+    when a slot and room in the 40 GB budget are free, its frames queued as
+    one request, and every step fires the next frames of all admitted streams.
+    Latency of a stream = observed completion of its last frame - arrival."""
+    from paper_1802_06625_b300.serve import Server
+
+    sw = synth.ServingWorkload(**{**synth.SERVING.__dict__, "streams": args.serve_streams})
+    specs = [sw.stream(i) for i in range(sw.streams)]
+    arr = sw.arrivals()
+    params = [(sw.taps(i).numpy(), sw.H(i).numpy()) for i in range(sw.streams)]
+    pool = sw.pool_tensor(device=dev)
+    fps = args.serve_fps
+    srv = Server(sw.B, sw.N, F_max=sw.F_hi, T_max=sw.T, max_streams=args.serve_slots,
+                 hbm_budget=int(args.serve_budget_gb * 2**30), frames_per_step=fps, ring=2 * fps,
+                 max_inflight=2, auto_release=True, device=dev.index)
+    # warm-up: one short stream end to end
+    sid = srv.open(specs[0]["F"], sw.T, specs[0]["tau"], *params[0])
+    srv.submit(sid, pool[:specs[0]["F"] * sw.B], n=2 * fps, period=1)
+    while srv.step():
+        pass
+    srv.sync()
+    srv.poll()
+    srv.close(sid)
+    srv.sync()
+
+    t0 = time.monotonic_ns()
+    due = [t0 + int(a * 1e9) for a in arr]
+    waiting, nxt, done_at, admitted_at, sid_of = [], 0, {}, {}, {}
+    peak_open, steps, entries = 0, 0, 0
+    while len(done_at) < sw.streams:
+        now = time.monotonic_ns()
+        while nxt < sw.streams and due[nxt] <= now:
+            waiting.append(nxt)
+            nxt += 1
+        while waiting:                                   # admission in arrival order
+            i = waiting[0]
+            sp = specs[i]
+            sid = srv.open(sp["F"], sw.T, sp["tau"], *params[i])
+            if sid is None:
+                break
+            waiting.pop(0)
+            sid_of[sid] = i
+            admitted_at[i] = time.monotonic_ns()
+            L = sp["F"] * sw.B
+            srv.submit(sid, pool[sp["offset"]:sp["offset"] + sp["period"] * L], n=sp["frames"], period=sp["period"])
+        peak_open = max(peak_open, len(sid_of))
+        n = srv.step()
+        if n:
+            steps += 1
+            entries += n
+        for sid, t_ns in srv.poll():
+            done_at[sid_of.pop(sid)] = t_ns
+            srv.close(sid)
+        if n == 0:
+            if sid_of:
+                srv.sync()                               # only steps in flight: wait for them
+            elif nxt < sw.streams:
+                time.sleep(max(0.0, (due[nxt] - time.monotonic_ns()) * 1e-9))
+    srv.sync()
+    t1 = max(done_at.values())
+    st = srv.stats()
+    srv.close_server()
+    lat = np.array([(done_at[i] - due[i]) * 1e-6 for i in range(sw.streams)])
+    wait = np.array([(admitted_at[i] - due[i]) * 1e-6 for i in range(sw.streams)])
+    samples = sum(sp["frames"] * sp["F"] * sw.B for sp in specs)
+    return {"workload": sw.name, "streams": sw.streams, "lambda_per_s": sw.lam,
+            "frames_per_stream": "log-uniform [10, 10^4]", "F": "uniform [64, 2048]",
+            "samples": samples, "Msamples_s": samples / ((t1 - t0) * 1e-9) / 1e6,
+            "makespan_s": (t1 - t0) * 1e-9,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "admission_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+            "steps": steps, "entries_per_step": entries / max(steps, 1), "peak_open_streams": peak_open,
+            "frames_per_step": fps, "hbm_budget_GB": args.serve_budget_gb, "slots": args.serve_slots,
+            "timing": "host monotonic clock; arrival = scheduled Poisson time, completion = when the host saw "
+                      "the stream's last step complete"}
 
 
 def run_e2e(args, w, dev, stream, rank, ws):
@@ -438,6 +521,11 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--serve-streams", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the top kernel")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -297,6 +297,93 @@ PRUNE_API prune_status prune_batch_pull(prune_batch *b, int32_t i, prune_frame_o
 PRUNE_API const char *prune_batch_last_error(const prune_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Request loop (serving): streams of frames arrive and leave at run time.
+ * Each admitted stream is one instance of the canonical graph whose
+ * parameters, delay token and result FIFO stay resident in device memory
+ * between requests; admission draws the stream's state from a fixed
+ * device-memory budget.  A step fires the next frames of every admitted
+ * stream that has queued frames and free result slots (the FIFO-space firing
+ * condition, Sec. IV), all streams together in the batched launches, so that
+ * streams that arrive while others are on the GPU join at the next step and
+ * their work shares the device with the rest.  Up to `max_inflight` steps are
+ * enqueued ahead of their completion.  One host thread per server.
+ * ---------------------------------------------------------------------- */
+
+typedef struct prune_server prune_server;
+
+#define PRUNE_SERVER_AUTO_RELEASE 1  /* completed frames leave the result FIFO without a pull */
+
+typedef struct prune_server_desc {
+  int32_t B;               /* block size common to all streams (as prune_graph_desc) */
+  int32_t N;               /* H size common to all streams; N = 64 runs HX on tensor cores */
+  int32_t F_max;           /* largest F a stream may have */
+  int32_t T_max;           /* largest T a stream may have */
+  int32_t max_streams;     /* streams admitted at once */
+  int32_t frames_per_step; /* frames one stream may advance per step (>= 1) */
+  int32_t ring;            /* result FIFO of a stream, in frames (>= frames_per_step) */
+  int32_t max_inflight;    /* steps enqueued ahead of completion (>= 1) */
+  uint64_t hbm_budget;     /* bytes of device memory for the streams' resident state */
+  void *stream;            /* cudaStream_t, or NULL for a stream owned by the server */
+  int32_t device;          /* CUDA device, -1 = current */
+  int32_t flags;           /* PRUNE_SERVER_* */
+} prune_server_desc;
+
+/* Allocates the budget as one device arena, the staging of max_inflight step
+ * tables and the status word.  EINVAL on a bad descriptor, ENOMEM when the
+ * device has no room for the budget. */
+PRUNE_API prune_status prune_server_create(const prune_server_desc *d, prune_server **out);
+/* Waits for the steps in flight and frees everything. */
+PRUNE_API prune_status prune_server_destroy(prune_server *s);
+
+/* Admit a stream with the parameters of g (F <= F_max, T <= T_max, B and N
+ * those of the server; taps and H host pointers, copied; g->stream, C and
+ * out_frames ignored).  PRUNE_EAGAIN, with nothing changed, when every slot is
+ * taken or the arena has no hole for the stream's state (retry after a
+ * close); the message then says which. */
+PRUNE_API prune_status prune_server_open(prune_server *s, const prune_graph_desc *g, int64_t *id);
+
+/* Queue n frames for stream id: frame q (0 <= q < n) is read at
+ * x + (q % period) * F*B complex64 samples (period >= 1; period = n for n
+ * distinct consecutive frames).  x device, 16-byte aligned, BORROWED: it must
+ * stay valid and unchanged until those frames are done (prune_server_progress). */
+PRUNE_API prune_status prune_server_submit(prune_server *s, int64_t id, const void *x, int64_t n, int64_t period);
+
+/* Enqueue one step.  Retires completed steps first, and waits for the oldest
+ * one when max_inflight are in flight.  *entries = frames fired by the step
+ * (0: nothing is ready; nothing enqueued). */
+PRUNE_API prune_status prune_server_step(prune_server *s, int32_t *entries);
+
+/* Frames of stream id: submitted and not yet fired, fired, done (their step
+ * completed), pulled (left the result FIFO).  Retires completed steps. */
+PRUNE_API prune_status prune_server_progress(prune_server *s, int64_t id, int64_t *queued, int64_t *fired,
+                                             int64_t *done, int64_t *pulled);
+
+/* Streams that became idle (nothing queued, every fired frame done) since the
+ * last call, each reported once per transition, with the host steady-clock
+ * time (ns) at which the completion was observed.  Retires completed steps. */
+PRUNE_API prune_status prune_server_poll(prune_server *s, int64_t *ids, int64_t *t_ns, int32_t max, int32_t *n);
+
+/* Oldest done frame of stream id out of its result FIFO: out->frame, out->c,
+ * and (mem HOST or DEVICE) c block indices into out->idx and c*B samples of
+ * the compacted HX output into out->y; with PRUNE_MEM_DISCARD only the slot is
+ * freed.  PRUNE_EAGAIN when no done frame is waiting. */
+PRUNE_API prune_status prune_server_pull(prune_server *s, int64_t id, prune_frame_out *out, int32_t mem);
+
+/* Leave: queued frames are dropped; the stream's memory and slot return to
+ * the server once its last step has completed. */
+PRUNE_API prune_status prune_server_close(prune_server *s, int64_t id);
+
+/* Wait for every step in flight; PRUNE_ETIMEOUT / PRUNE_EDEVICE on a
+ * device-side failure recorded by a kernel. */
+PRUNE_API prune_status prune_server_sync(prune_server *s);
+
+/* Arena bytes in use and in all, open streams, steps enqueued so far. */
+PRUNE_API prune_status prune_server_stats(prune_server *s, uint64_t *hbm_used, uint64_t *hbm_budget,
+                                          int32_t *open, int64_t *steps);
+
+PRUNE_API const char *prune_server_last_error(const prune_server *s);
+
+/* ------------------------------------------------------------------------
  * Adjoints over a recorded control trace (training the taps and H).  The
  * decisions v[b] = E_b > tau are piecewise constant in the parameters, so
  * with the trace (c, idx) of a forward firing held fixed the sink output is

@@ -27,7 +27,11 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_fifo_capacity_of", "prune_last_error", "prune_profile", "prune_kernel_times", "prune_fir_energy", "prune_det_sel", "prune_hx",
            "prune_fire_frames_noalloc", "prune_batch_create", "prune_batch_destroy", "prune_batch_offset",
            "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error",
-           "prune_hx_adjoint", "prune_fir_adjoint")
+           "prune_hx_adjoint", "prune_fir_adjoint",
+           "prune_server_create", "prune_server_destroy", "prune_server_open", "prune_server_submit",
+           "prune_server_step", "prune_server_progress", "prune_server_poll", "prune_server_pull",
+           "prune_server_close", "prune_server_sync", "prune_server_stats", "prune_server_last_error")
+PRUNE_SERVER_AUTO_RELEASE = 1
 PRUNE_BATCH_GRAPH = 1
 
 
@@ -43,6 +47,12 @@ class prune_frame_out(ctypes.Structure):
 
 class prune_frame_view(ctypes.Structure):
     _fields_ = [("frame", I64), ("c", I32), ("reserved", I32), ("idx", P), ("y", P)]
+
+
+class prune_server_desc(ctypes.Structure):
+    _fields_ = [("B", I32), ("N", I32), ("F_max", I32), ("T_max", I32), ("max_streams", I32),
+                ("frames_per_step", I32), ("ring", I32), ("max_inflight", I32), ("hbm_budget", U64),
+                ("stream", P), ("device", I32), ("flags", I32)]
 
 
 class PruneError(RuntimeError):
@@ -87,6 +97,19 @@ def load(path: str | None = None):
         "prune_batch_pull": [P, I32, ctypes.POINTER(prune_frame_out), I32],
         "prune_hx_adjoint": [P, P, P, I32, I32, I32, I32, P, P, P, P, P],
         "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
+        "prune_server_create": [ctypes.POINTER(prune_server_desc), ctypes.POINTER(P)],
+        "prune_server_destroy": [P],
+        "prune_server_open": [P, ctypes.POINTER(prune_graph_desc), ctypes.POINTER(I64)],
+        "prune_server_submit": [P, I64, P, I64, I64],
+        "prune_server_step": [P, ctypes.POINTER(I32)],
+        "prune_server_progress": [P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                  ctypes.POINTER(I64)],
+        "prune_server_poll": [P, ctypes.POINTER(I64), ctypes.POINTER(I64), I32, ctypes.POINTER(I32)],
+        "prune_server_pull": [P, I64, ctypes.POINTER(prune_frame_out), I32],
+        "prune_server_close": [P, I64],
+        "prune_server_sync": [P],
+        "prune_server_stats": [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(I32),
+                               ctypes.POINTER(I64)],
     })
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -96,6 +119,8 @@ def load(path: str | None = None):
     lib.prune_last_error.restype = ctypes.c_char_p
     lib.prune_batch_last_error.argtypes = [P]
     lib.prune_batch_last_error.restype = ctypes.c_char_p
+    lib.prune_server_last_error.argtypes = [P]
+    lib.prune_server_last_error.restype = ctypes.c_char_p
     return lib
 
 
@@ -109,9 +134,11 @@ def lib():
     return _LIB
 
 
-def check(status: int, g=None, batch=None):
+def check(status: int, g=None, batch=None, server=None):
     if status != PRUNE_OK:
-        if batch is not None:
+        if server is not None:
+            msg = lib().prune_server_last_error(server).decode(errors="replace")
+        elif batch is not None:
             msg = lib().prune_batch_last_error(batch).decode(errors="replace")
         else:
             msg = lib().prune_last_error(g).decode(errors="replace")

@@ -70,17 +70,7 @@ prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   bp.hx_items = b->hx_items;
   bp.timeout_ns = 2000000000ull;
   bp.status = b->status;
-  batch_fir_kernel<<<b->fir_tiles, kFirThreads, fir_smem_bytes(b->tp_max), b->stream>>>(bp, b->tp_max);
-  batch_detsel_kernel<<<b->n, kDetThreads, 0, b->stream>>>(bp);
-  if (b->N == kTcNc) {
-    const int grid = std::max(1, std::min(b->hx_items, b->sms));
-    batch_hx_tc_kernel<<<grid, kTcThreads, kTcSmemBytes, b->stream>>>(bp);
-  } else {
-    const int grid = std::max(1, std::min(b->hx_items, b->sms * 8));
-    const size_t smem = (static_cast<size_t>(b->B) + static_cast<size_t>(b->N) * b->N) * sizeof(float2);
-    batch_hx_cuda_kernel<<<grid, kHxThreads, smem, b->stream>>>(bp);
-  }
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = batch_launch_step(bp, b->tp_max, b->sms, b->stream);
   if (e != cudaSuccess) return bfail(b, PRUNE_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return PRUNE_OK;
 }
@@ -222,18 +212,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
                        b->stream) == cudaSuccess &&
        cudaMemcpyAsync(b->hx_map, hx_map.data(), sizeof(int32_t) * hx_map.size(), cudaMemcpyHostToDevice,
                        b->stream) == cudaSuccess;
-  if (ok && fir_smem_bytes(b->tp_max) > 48 * 1024)
-    ok = cudaFuncSetAttribute(batch_fir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(fir_smem_bytes(b->tp_max))) == cudaSuccess;
-  if (ok && N == kTcNc)
-    ok = cudaFuncSetAttribute(batch_hx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(kTcSmemBytes)) == cudaSuccess;
-  if (ok && N != kTcNc) {
-    const size_t smem = (static_cast<size_t>(B) + static_cast<size_t>(N) * N) * sizeof(float2);
-    if (smem > 48 * 1024)
-      ok = cudaFuncSetAttribute(batch_hx_cuda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem)) == cudaSuccess;
-  }
+  ok = ok && batch_enable_smem(b->tp_max, B, N);
   if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) {
     b->err = std::string("batch upload failed: ") + cudaGetErrorString(cudaGetLastError());
     return bail(PRUNE_ECUDA);

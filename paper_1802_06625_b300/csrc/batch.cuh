@@ -4,6 +4,8 @@
 // Instances are independent DPGs (Sec. V), so the batch is a union of
 // graphs; every instance keeps its own delay token across steps.
 #pragma once
+#include <algorithm>
+
 #include "detsel.cuh"
 #include "fir.cuh"
 #include "hx_tc.cuh"
@@ -12,10 +14,13 @@ namespace prune {
 
 struct BatchInst {
   int64_t x_off;          // offset of this instance's frame in the step's input (samples)
+  const float2 *x;        // or, when not null, the frame itself (request-loop entries)
   const float2 *taps;     // T taps
   const float2 *H;        // N x N
   const uint16_t *bops;   // tensor-core HX operands (N = 64) or nullptr
-  float2 *hist;           // [2][T-1] delay token, double buffered by step parity
+  float2 *hist;           // [2][T-1] delay token, double buffered by step parity; when null:
+  const float2 *hist_in;  //   the token before the frame (null = zeros), and
+  float2 *hist_out;       //   where the token after the frame goes (null = not kept)
   float2 *y;              // FIR output frame, F*B
   float *energy;          // F
   int32_t *c;             // 1: selected blocks
@@ -51,8 +56,9 @@ static __global__ void __launch_bounds__(kFirThreads) batch_fir_kernel(BatchPara
   const int64_t L = static_cast<int64_t>(in.F) * bp.B;
   const int64_t s0 = static_cast<int64_t>(gt - in.fir_tile0) * bp.TS;
   const int nv = static_cast<int>(min(static_cast<int64_t>(bp.TS), L - s0));
-  const float2 *cur = bp.x + in.x_off;
-  const float2 *hist = in.T > 1 ? in.hist + bp.parity * (in.T - 1) : nullptr;
+  const float2 *cur = in.x ? in.x : bp.x + in.x_off;
+  const float2 *hist = in.T <= 1 ? nullptr : in.hist ? in.hist + bp.parity * (in.T - 1) : in.hist_in;
+  float2 *hout = in.T <= 1 ? nullptr : in.hist ? in.hist + (1 - bp.parity) * (in.T - 1) : in.hist_out;
   for (int t = tid; t < TP; t += kFirThreads) hs[t] = t < in.T ? in.taps[t] : make_float2(0.f, 0.f);
   fir_stage_window(xs, cur, nullptr, hist, L, in.T, TP, s0, nv, tid);
   __syncthreads();
@@ -60,8 +66,7 @@ static __global__ void __launch_bounds__(kFirThreads) batch_fir_kernel(BatchPara
   fir_compute(xs, hs, TP, tid, acc);
   fir_block_energies(acc, bp.B, nv, tid, red, Et);
   if (tid < nv / bp.B) in.energy[s0 / bp.B + tid] = Et[tid];
-  if (in.T > 1 && s0 + nv == L) {  // next delay token: the last T-1 input samples
-    float2 *hout = in.hist + (1 - bp.parity) * (in.T - 1);
+  if (hout && s0 + nv == L) {  // next delay token: the last T-1 input samples
     for (int m = tid; m < in.T - 1; m += kFirThreads) hout[m] = xs[pad_idx(TP - 1 + nv - (in.T - 1) + m)];
   }
   __syncthreads();
@@ -269,6 +274,43 @@ static __global__ void __launch_bounds__(kTcThreads, 1) batch_hx_tc_kernel(Batch
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
   }
+}
+
+// The three launches of one step over the instances of `bp` (the batch and
+// the request loop share them).  Dynamic shared memory above 48 KB must have
+// been enabled on these kernels in the calling translation unit
+// (batch_enable_smem).
+static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, int sms, cudaStream_t stream) {
+  batch_fir_kernel<<<bp.fir_tiles, kFirThreads, fir_smem_bytes(tp_max), stream>>>(bp, tp_max);
+  batch_detsel_kernel<<<bp.n, kDetThreads, 0, stream>>>(bp);
+  if (bp.N == kTcNc) {
+    const int grid = std::max(1, std::min(bp.hx_items, sms));
+    batch_hx_tc_kernel<<<grid, kTcThreads, kTcSmemBytes, stream>>>(bp);
+  } else {
+    const int grid = std::max(1, std::min(bp.hx_items, sms * 8));
+    const size_t smem = (static_cast<size_t>(bp.B) + static_cast<size_t>(bp.N) * bp.N) * sizeof(float2);
+    batch_hx_cuda_kernel<<<grid, kHxThreads, smem, stream>>>(bp);
+  }
+  return cudaGetLastError();
+}
+
+// Opt the step kernels of this translation unit into the dynamic shared
+// memory that taps of up to tp_max (padded) and the given B, N need.
+static inline bool batch_enable_smem(int tp_max, int B, int N) {
+  bool ok = true;
+  if (fir_smem_bytes(tp_max) > 48 * 1024)
+    ok = cudaFuncSetAttribute(batch_fir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(fir_smem_bytes(tp_max))) == cudaSuccess;
+  if (ok && N == kTcNc)
+    ok = cudaFuncSetAttribute(batch_hx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kTcSmemBytes)) == cudaSuccess;
+  if (ok && N != kTcNc) {
+    const size_t smem = (static_cast<size_t>(B) + static_cast<size_t>(N) * N) * sizeof(float2);
+    if (smem > 48 * 1024)
+      ok = cudaFuncSetAttribute(batch_hx_cuda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)) == cudaSuccess;
+  }
+  return ok;
 }
 
 }  // namespace prune

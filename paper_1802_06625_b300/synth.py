@@ -30,7 +30,7 @@ GOLDEN = 0x9E3779B97F4A7C15
 _C1 = 0xBF58476D1CE4E5B9
 _C2 = 0x94D049BB133111EB
 
-TAG_X, TAG_TAPS, TAG_H, TAG_BURST, TAG_FRAC, TAG_TAU, TAG_SHAPE = 1, 2, 3, 4, 5, 6, 7
+TAG_X, TAG_TAPS, TAG_H, TAG_BURST, TAG_FRAC, TAG_TAU, TAG_SHAPE, TAG_ARRIVAL = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 def mix64(z: int) -> int:
@@ -219,3 +219,66 @@ class BatchedWorkload:
 # 512 instances, F log-uniform in [16, 4096], B = 256, T in {8, 32, 128},
 # H 64x64 per instance.
 BATCHED = BatchedWorkload("batched_512x_B256_N64", instances=512, B=256, N=64, seed=3)
+
+
+@dataclass
+class ServingWorkload:
+    """Streams of frames arriving as a Poisson process of rate ``lam`` per
+    second (exponential inter-arrival times): frames per stream a log-uniform
+    integer in [fr_lo, fr_hi], F a uniform integer in [F_lo, F_hi], common B,
+    T and N, tau = kappa * B with kappa ~ U(kappa_lo, kappa_hi), taps and H per
+    stream.  The frames are read from a device-resident pool of ``pool``
+    frames of F_hi * B samples (pool frame k has burst fraction U(p_lo, p_hi)):
+    stream i reads F*B-sample frames cyclically, period up to 8, from its own
+    offset into the flat pool."""
+    name: str
+    streams: int
+    lam: float
+    B: int
+    T: int
+    N: int
+    seed: int
+    fr_lo: int = 10
+    fr_hi: int = 10000
+    F_lo: int = 64
+    F_hi: int = 2048
+    p_lo: float = 0.05
+    p_hi: float = 0.95
+    kappa_lo: float = 2.0
+    kappa_hi: float = 8.0
+    pool: int = 16
+
+    def stream(self, i: int) -> dict:
+        u = uniform(stream_key(self.seed, TAG_SHAPE, i), 0, 3)
+        lf = math.log(self.fr_lo) + float(u[0]) * (math.log(self.fr_hi + 1) - math.log(self.fr_lo))
+        frames = max(self.fr_lo, min(self.fr_hi, int(math.floor(math.exp(lf)))))
+        F = self.F_lo + min(int(float(u[1]) * (self.F_hi - self.F_lo + 1)), self.F_hi - self.F_lo)
+        kappa = self.kappa_lo + (self.kappa_hi - self.kappa_lo) * float(u[2])
+        L, plen = F * self.B, self.pool * self.F_hi * self.B
+        off = ((i * 7919) % self.pool) * self.F_hi * self.B
+        period = max(1, min(8, (plen - off) // L))
+        return {"F": F, "frames": frames, "tau": float(kappa * self.B), "offset": off, "period": period}
+
+    def arrivals(self) -> list:
+        """Arrival times in seconds from 0 (cumulative exponential draws)."""
+        u = uniform(stream_key(self.seed, TAG_ARRIVAL), 0, self.streams)
+        return torch.cumsum(-torch.log(u) / self.lam, 0).tolist()
+
+    def taps(self, i: int, device="cpu"):
+        return taps(self.seed, self.T, i, device)
+
+    def H(self, i: int, device="cpu"):
+        return hmat(self.seed, self.N, i, device)
+
+    def pool_tensor(self, device="cpu") -> torch.Tensor:
+        """The frame pool, flat complex64 [pool * F_hi * B]."""
+        out = []
+        for k in range(self.pool):
+            p = self.p_lo + (self.p_hi - self.p_lo) * frame_uniform(self.seed, TAG_FRAC, -1, k)
+            out.append(frame(self.seed, self.F_hi, self.B, p, -1, k, device).reshape(-1))
+        return torch.cat(out)
+
+
+# Streams arriving at 2000/s, 10..10^4 frames each, F in [64, 2048],
+# B = 512, T = 32, H 64x64 per stream.
+SERVING = ServingWorkload("serving_poisson2000_B512_T32_N64", streams=256, lam=2000.0, B=512, T=32, N=64, seed=5)
