@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 from paper_1802_06625_b300 import synth  # noqa: E402
 
 METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 latency"
+# DRAM bytes (read + write) per frame of the 4096 x 1024 workload, per kernel
+# kind, from one ncu capture of the kernel as it stands (8-frame launch,
+# dram__bytes_read.sum + dram__bytes_write.sum divided by 8); scaled to a
+# launch by the frames it fires.  Remove an entry when its kernel changes.
+TRAFFIC_PER_FRAME = {6: 362.63e6 / 8}
 UNIT = "Msamples/s"
 # FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
 # FP32 lanes x 2 flop x 2.032 GHz.
@@ -281,7 +286,10 @@ def run_ours(args, w):
                                   "note": "FP16 MMA work incl. the 3 split passes; peak = measured BF16 sustained "
                                           "(FP16 has the same nominal rate)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = args.traffic
+        traffic = args.traffic
+        if traffic is None and kind in TRAFFIC_PER_FRAME and w.name == synth.PLAIN_LARGE.name:
+            traffic = TRAFFIC_PER_FRAME[kind] * frames_per_launch
+        roof["traffic"] = traffic
         roof["kernel"] = KIND_NAMES[kind]
         roof["avg_launch_ms"] = kms / kn
         roof["share"] = kms / max(sum(t for t, _ in times.values()), 1e-12)
