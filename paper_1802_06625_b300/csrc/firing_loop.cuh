@@ -135,50 +135,115 @@ __device__ __forceinline__ int64_t lookback_warp(const LoopParams &p, uint64_t *
   return static_cast<int64_t>(prefix);
 }
 
-// Per-frame FIFO bookkeeping of every actor's firing (single thread).
-__device__ __forceinline__ void frame_bookkeeping(const LoopParams &p, uint64_t frame, uint32_t c) {
-  const uint64_t F = p.f.F;
-  uint32_t *st = p.status;
-  fifo_release(p.ctr, 0, F, 0, st, kActFir, frame);
-  fifo_release(p.ctr, 1, 1, 1, st, kActFir, frame);
-  fifo_commit(p.ctr, 1, 1, 1, p.cap[1], st, kActFir, frame);
-  fifo_commit(p.ctr, 2, F, 0, p.cap[2], st, kActFir, frame);
-  fifo_commit(p.ctr, 3, F, 0, p.cap[3], st, kActFir, frame);
-  fifo_release(p.ctr, 2, F, 0, st, kActDet, frame);
-  fifo_commit(p.ctr, 4, 1, 0, p.cap[4], st, kActDet, frame);
-  fifo_commit(p.ctr, 5, 1, 0, p.cap[5], st, kActDet, frame);
-  fifo_release(p.ctr, 4, 1, 0, st, kActSel, frame);
-  fifo_release(p.ctr, 3, F, 0, st, kActSel, frame);
-  fifo_commit(p.ctr, 6, c, 0, p.cap[6], st, kActSel, frame);
-  fifo_release(p.ctr, 6, c, 0, st, kActHx, frame);
-  fifo_commit(p.ctr, 7, c, 0, p.cap[7], st, kActHx, frame);
-  fifo_release(p.ctr, 5, 1, 0, st, kActSink, frame);
-  fifo_release(p.ctr, 7, c, 0, st, kActSink, frame);
+// Register copy of the FIFO counters (written, read, peak per FIFO).
+struct CtrCopy {
+  uint64_t w[kNumFifos], r[kNumFifos], pk[kNumFifos];
+};
+
+// The checks of fifo_release / fifo_commit, on the register copy.
+__device__ __forceinline__ void book_release(CtrCopy &m, int f, uint64_t n, uint64_t delay, uint32_t *st,
+                                             uint32_t actor, uint64_t frame) {
+  if (st && delay + m.w[f] < m.r[f] + n) report_error(st, kDevUnderflow, actor, static_cast<uint32_t>(f), frame);
+  m.r[f] += n;
+}
+__device__ __forceinline__ void book_commit(CtrCopy &m, int f, uint64_t n, uint64_t delay, uint64_t cap,
+                                            uint32_t *st, uint32_t actor, uint64_t frame) {
+  m.w[f] += n;
+  const uint64_t occ = delay + m.w[f] - m.r[f];
+  if (occ > m.pk[f]) m.pk[f] = occ;
+  if (st && occ > cap) report_error(st, kDevOverflow, actor, static_cast<uint32_t>(f), frame);
 }
 
-// Book finished frames in frame order: frames finish out of order, but the
-// f1 token of frame j+1 is the one frame j produced.  Lock-free: a thread that
-// cannot take the lock leaves, and the holder re-checks after releasing it,
-// so every ready frame is booked by someone.  No thread ever waits.
-__device__ __forceinline__ void drain_bookkeeping(const LoopParams &p, uint64_t seq_end) {
+// Per-frame FIFO bookkeeping of every actor's firing, in the actors' order
+// (st = nullptr: counters only, no reports).
+__device__ __forceinline__ void frame_bookkeeping(const LoopParams &p, CtrCopy &m, uint64_t frame, uint32_t c,
+                                                  uint32_t *st) {
+  const uint64_t F = p.f.F;
+  book_release(m, 0, F, 0, st, kActFir, frame);
+  book_release(m, 1, 1, 1, st, kActFir, frame);
+  book_commit(m, 1, 1, 1, p.cap[1], st, kActFir, frame);
+  book_commit(m, 2, F, 0, p.cap[2], st, kActFir, frame);
+  book_commit(m, 3, F, 0, p.cap[3], st, kActFir, frame);
+  book_release(m, 2, F, 0, st, kActDet, frame);
+  book_commit(m, 4, 1, 0, p.cap[4], st, kActDet, frame);
+  book_commit(m, 5, 1, 0, p.cap[5], st, kActDet, frame);
+  book_release(m, 4, 1, 0, st, kActSel, frame);
+  book_release(m, 3, F, 0, st, kActSel, frame);
+  book_commit(m, 6, c, 0, p.cap[6], st, kActSel, frame);
+  book_release(m, 6, c, 0, st, kActHx, frame);
+  book_commit(m, 7, c, 0, p.cap[7], st, kActHx, frame);
+  book_release(m, 5, 1, 0, st, kActSink, frame);
+  book_release(m, 7, c, 0, st, kActSink, frame);
+}
+
+// Book finished frames in frame order, by one warp (all 32 lanes enter):
+// frames finish out of order, but the f1 token of frame j+1 is the one frame
+// j produced.  Lock-free: a warp that cannot take the lock leaves, and the
+// holder re-checks after releasing it, so every ready frame is booked by
+// someone; no thread ever waits.  The holder reads the counters once, reads
+// the ready flags and SINK counts of 32 frames per round trip, replays the
+// per-frame bookkeeping on a register copy (the same checks, in the same
+// order) and adds each counter's change with one atomic.  f0's `written` is
+// also bumped by pushes meanwhile, so it is only read (frames were pushed
+// before they fired).
+__device__ __forceinline__ void drain_bookkeeping(const LoopParams &p, uint64_t seq_end, int lane) {
   for (;;) {
-    if (atomicCAS(&p.ls->book_lock, 0u, 1u) != 0u) return;
+    int got = 0;
+    if (lane == 0) got = atomicCAS(&p.ls->book_lock, 0u, 1u) == 0u;
+    if (!__shfl_sync(0xffffffffu, got, 0)) return;
     __threadfence();
+    const uint64_t j0 = *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked);
+    const uint64_t cv = lane < 3 * kNumFifos ? ld_acquire_u64(&p.ctr[lane]) : 0ull;
+    CtrCopy m;
+#pragma unroll
+    for (int f = 0; f < kNumFifos; ++f) {
+      m.w[f] = __shfl_sync(0xffffffffu, cv, 3 * f + kCtrWritten);
+      m.r[f] = __shfl_sync(0xffffffffu, cv, 3 * f + kCtrRead);
+      m.pk[f] = __shfl_sync(0xffffffffu, cv, 3 * f + kCtrPeak);
+    }
+    uint64_t j = j0;
     for (;;) {
-      const uint64_t j = *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked);
-      if (j >= seq_end) break;
-      const int64_t slot = static_cast<int64_t>(j % static_cast<uint64_t>(p.C));
-      if (ld_acquire_u64(&p.ready[slot]) != j + 1) break;
-      const int64_t rs = static_cast<int64_t>(j % static_cast<uint64_t>(p.rslot.cap));
-      frame_bookkeeping(p, j, static_cast<uint32_t>(*reinterpret_cast<volatile int32_t *>(&p.rec_c[rs])));
-      *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked) = j + 1;
+      const uint64_t jj = j + static_cast<uint64_t>(lane);
+      bool rdy = false;
+      uint32_t c = 0;
+      if (jj < seq_end) {
+        rdy = ld_acquire_u64(&p.ready[static_cast<int64_t>(jj % static_cast<uint64_t>(p.C))]) == jj + 1;
+        if (rdy)
+          c = static_cast<uint32_t>(
+              *reinterpret_cast<volatile int32_t *>(&p.rec_c[static_cast<int64_t>(jj % static_cast<uint64_t>(p.rslot.cap))]));
+      }
+      const unsigned notr = __ballot_sync(0xffffffffu, !rdy);
+      const int nr = notr ? __ffs(notr) - 1 : 32;  // ready frames in a row from j
+      for (int i = 0; i < nr; ++i) {
+        const uint32_t ci = __shfl_sync(0xffffffffu, c, i);
+        frame_bookkeeping(p, m, j + static_cast<uint64_t>(i), ci, lane == 0 ? p.status : nullptr);
+      }
+      j += static_cast<uint64_t>(nr);
+      if (nr < 32) break;
+    }
+    if (j > j0) {
+#pragma unroll
+      for (int f = 0; f < kNumFifos; ++f) {
+        unsigned long long *c3 = reinterpret_cast<unsigned long long *>(p.ctr + 3 * f);
+        if (f != 0 && lane == 3 * f + kCtrWritten && m.w[f] > cv) atomicAdd(&c3[kCtrWritten], m.w[f] - cv);
+        if (lane == 3 * f + kCtrRead && m.r[f] > cv) atomicAdd(&c3[kCtrRead], m.r[f] - cv);
+        if (lane == 3 * f + kCtrPeak && m.pk[f] > cv) atomicMax(&c3[kCtrPeak], m.pk[f]);
+      }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked) = j;
     }
     __threadfence();
-    atomicExch(&p.ls->book_lock, 0u);
+    __syncwarp();
+    if (lane == 0) atomicExch(&p.ls->book_lock, 0u);
     __threadfence();
-    const uint64_t j = *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked);
-    if (j >= seq_end) return;
-    if (ld_acquire_u64(&p.ready[static_cast<int64_t>(j % static_cast<uint64_t>(p.C))]) != j + 1) return;
+    int again = 0;
+    if (lane == 0) {
+      const uint64_t jb = *reinterpret_cast<volatile unsigned long long *>(&p.ls->booked);
+      again = jb < seq_end &&
+              ld_acquire_u64(&p.ready[static_cast<int64_t>(jb % static_cast<uint64_t>(p.C))]) == jb + 1;
+    }
+    if (!__shfl_sync(0xffffffffu, again, 0)) return;
   }
 }
 
@@ -350,22 +415,27 @@ __global__ void __launch_bounds__(kFirThreads) firing_loop_kernel(LoopParams p) 
       }
     }
 
-    // 6. frame completion: the last tile to finish writes the SINK record
+    // 6. frame completion: the last tile to finish writes the SINK record;
+    //    warp 0 then books the frames that are ready in order
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const uint32_t old = atomicAdd(&p.done[fslot], 1u);
-      if (old + 1u == static_cast<uint32_t>(f.tiles)) {
-        p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
-        const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
-        const uint32_t c = static_cast<uint32_t>(w);
-        p.rec_c[rs] = static_cast<int32_t>(c);
-        p.rec_frame[rs] = static_cast<int64_t>(seq);
+    if (tid < 32) {
+      int last = 0;
+      if (tid == 0) {
         __threadfence();
-        st_release_u64(&p.ready[fslot], seq + 1);
-        __threadfence();
-        drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames);
+        const uint32_t old = atomicAdd(&p.done[fslot], 1u);
+        if (old + 1u == static_cast<uint32_t>(f.tiles)) {
+          p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
+          const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
+          const uint32_t c = static_cast<uint32_t>(w);
+          p.rec_c[rs] = static_cast<int32_t>(c);
+          p.rec_frame[rs] = static_cast<int64_t>(seq);
+          __threadfence();
+          st_release_u64(&p.ready[fslot], seq + 1);
+          __threadfence();
+          last = 1;
+        }
       }
+      if (__shfl_sync(0xffffffffu, last, 0)) drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames, tid);
     }
   }
   // every CTA makes exactly one failing claim, unless it left early

@@ -26,8 +26,8 @@
 //
 // Control: block energies from the FIR accumulators, v[b] = E_b > tau, warp
 // ballot compaction in the tile and the warp-parallel decoupled look-back of
-// the CUDA-core firing loop across tiles; the last tile of a frame writes the
-// SINK record and books the FIFO counters in frame order.  All waits are
+// the CUDA-core firing loop across tiles (frames interleaved, see
+// tc_ticket_tile); the last tile of a frame writes the SINK record and books the FIFO counters in frame order.  All waits are
 // bounded; tensor memory is freed on every path.
 #pragma once
 #include "firing_loop.cuh"
@@ -108,6 +108,7 @@ __host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const floa
 }
 
 struct TcLoopParams {
+  int32_t window;        // frames fired round-robin (tc_ticket_tile)
   LoopParams lp;
   const uint16_t *fir_ops;
   const uint16_t *hx_ops;
@@ -127,6 +128,24 @@ __device__ __forceinline__ uint4 split_pack8(const float *v, bool lo) {
     w[e] = static_cast<uint32_t>(__half_as_ushort(a)) | (static_cast<uint32_t>(__half_as_ushort(b)) << 16);
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Order of the work items.  Tickets are claimed in order; ticket t maps to
+// a (frame, tile) pair so that a window of up to W frames is fired
+// round-robin: consecutive tickets go to different frames, and the tiles of
+// one frame are claimed W tickets apart, in increasing order.  With P
+// pipelines in flight a frame then has about P / W tiles in flight, so the
+// look-back of a tile rarely finds an unpublished predecessor (with W = 1
+// every pipeline would work on the same frame and each look-back would wait
+// for the slowest of hundreds of tiles).
+__host__ __device__ __forceinline__ void tc_ticket_tile(unsigned long long t, int frames, int tiles, int W, int *k,
+                                                        int *tile) {
+  const unsigned long long win = static_cast<unsigned long long>(W) * tiles;
+  const int w = static_cast<int>(t / win);
+  const int r = static_cast<int>(t % win);
+  const int wc = min(W, frames - w * W);  // frames in this window
+  *k = w * W + r % wc;
+  *tile = r / wc;
 }
 
 template <int NP>
@@ -150,11 +169,12 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   int32_t *s_flag = reinterpret_cast<int32_t *>(misc + 16);
   int32_t *s_cnt = reinterpret_cast<int32_t *>(misc + 20);
   unsigned long long *s_ticket = reinterpret_cast<unsigned long long *>(misc + 24);
-  long long *s_prefix = reinterpret_cast<long long *>(misc + 40);
   int32_t *s_rank = reinterpret_cast<int32_t *>(misc + 64);          // [128] blocks of a tile
   float *eth = reinterpret_cast<float *>(misc + 576);                 // [128] chunk energies
   float *Et = eth + 128;                                              // [128] block energies
   float *red4 = Et + 128;                                             // [4]
+  int32_t *s_rule = reinterpret_cast<int32_t *>(misc + 36);           // firing rule of the claimed tile
+  long long *s_prefix = reinterpret_cast<long long *>(misc + 40);
   uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 32);
 
   const int tid = cta_tid % kTPipeThreads, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
@@ -198,35 +218,56 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   const int npieces = (kTGroups + S) * 64;     // 16-byte pieces of the chunk array
   uint64_t f0_seen = 0;                        // thread 0: last f0 counter value read
   bool fir_pending = false, hx_pending = false;
-  for (;;) {
-    if (tid == 0) {
-      const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
-      *s_ticket = ld_volatile_u32(&p.ls->abort) ? ~0ull : tk;
+  // Tickets are claimed in order by all P = grid x NP pipelines, so the tile
+  // of ticket t + P is claimed about one tile period after t.  The claiming
+  // thread (thread 32 of the pipeline, while thread 0 books the previous
+  // tile) prefetches that tile's input into L2 when its frame is already
+  // written, so the loads of the tile that follows hit in L2; then it checks
+  // FIR's firing rule on f0 for the claimed tile (bounded wait).
+  const unsigned long long P = static_cast<unsigned long long>(gridDim.x) * NP;
+  auto claim = [&]() {
+    const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
+    int rule = 0;
+    if (tk < total) {
+      int kc, tc;
+      tc_ticket_tile(tk, f.frames, f.tiles, tp.window, &kc, &tc);
+      const uint64_t need = (static_cast<uint64_t>(f.yslot.seq0) + kc + 1) * static_cast<uint64_t>(f.F);
+      if (f0_seen < need) {
+        const bool ok = bounded_wait(p, [&] {
+          f0_seen = ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]);
+          return f0_seen >= need;
+        }, kActFir, 0, static_cast<uint64_t>(f.yslot.seq0) + kc);
+        rule = ok ? 0 : -1;
+      }
+      const unsigned long long u = tk + P;
+      if (u < total) {
+        int kn, tn;
+        tc_ticket_tile(u, f.frames, f.tiles, tp.window, &kn, &tn);
+        const uint64_t needn = (static_cast<uint64_t>(f.yslot.seq0) + kn + 1) * static_cast<uint64_t>(f.F);
+        if (f0_seen >= needn) {  // frame written: its slot holds it
+          const int64_t s0n = static_cast<int64_t>(tn) * kTTile;
+          const int64_t lo = s0n >= static_cast<int64_t>(S) * kTR ? s0n - static_cast<int64_t>(S) * kTR : 0;
+          const int64_t hi = min(s0n + static_cast<int64_t>(kTTile), f.L);
+          const float2 *src = f.src.frame(kn) + lo;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(static_cast<uint32_t>((hi - lo) * 8))
+                       : "memory");
+        }
+      }
     }
-    psync();
+    *s_rule = rule;
+    *s_ticket = ld_volatile_u32(&p.ls->abort) ? ~0ull : tk;
+  };
+  if (tid == 32) claim();
+  psync();
+  for (;;) {
     const unsigned long long t = *s_ticket;
-    if (t >= total) break;
-    const int k = static_cast<int>(t / f.tiles);
-    const int tile = static_cast<int>(t % f.tiles);
+    if (t >= total || *s_rule < 0) break;
+    int k, tile;
+    tc_ticket_tile(t, f.frames, f.tiles, tp.window, &k, &tile);
     const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
     const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
     const int nv = static_cast<int>(min(static_cast<int64_t>(kTTile), f.L - s0));
     const int rows_valid = nv / kTR;
-
-    // firing rule of FIR on f0 (device counter, bounded wait; read again only
-    // when a frame beyond the last value seen is needed)
-    if (tid == 0) {
-      const uint64_t need = (seq + 1) * static_cast<uint64_t>(f.F);
-      bool ok = true;
-      if (f0_seen < need)
-        ok = bounded_wait(p, [&] {
-          f0_seen = ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]);
-          return f0_seen >= need;
-        }, kActFir, 0, seq);
-      *s_cnt = ok ? 0 : -1;
-    }
-    psync();
-    if (*s_cnt < 0) break;
 
     // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g.
     // A thread's global loads are issued in batches before conversion.
@@ -467,23 +508,30 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
       }
     }
 
-    // ---- frame completion: the last tile to finish writes the SINK record
+    // ---- frame completion: the last tile to finish writes the SINK record;
+    // warp 0 then books the frames that are ready in order
     tc_fence_before();
     psync();
-    if (tid == 0) {
-      __threadfence();
-      const uint32_t old = atomicAdd(&p.done[fslot], 1u);
-      if (old + 1u == static_cast<uint32_t>(f.tiles)) {
-        p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
-        const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
-        p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
-        p.rec_frame[rs] = static_cast<int64_t>(seq);
+    if (warp == 0) {
+      int last = 0;
+      if (lane == 0) {
         __threadfence();
-        st_release_u64(&p.ready[fslot], seq + 1);
-        __threadfence();
-        drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames);
+        const uint32_t old = atomicAdd(&p.done[fslot], 1u);
+        if (old + 1u == static_cast<uint32_t>(f.tiles)) {
+          p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
+          const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
+          p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
+          p.rec_frame[rs] = static_cast<int64_t>(seq);
+          __threadfence();
+          st_release_u64(&p.ready[fslot], seq + 1);
+          __threadfence();
+          last = 1;
+        }
       }
+      if (__shfl_sync(0xffffffffu, last, 0)) drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames, lane);
     }
+    if (tid == 32) claim();
+    psync();
   }
 
   // leave: let MMAs still in flight land (bounded) before freeing tensor memory

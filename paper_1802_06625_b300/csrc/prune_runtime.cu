@@ -365,6 +365,8 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
     // one CTA per SM, np tile pipelines in each
     const int grid = static_cast<int>(std::max<unsigned long long>(
         1, std::min<unsigned long long>((ttotal + np - 1) / np, static_cast<unsigned long long>(g->sms))));
+    // frames fired round-robin: about 8 tiles of one frame in flight
+    tp.window = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(n, (grid * np + 7) / 8)));
     cudaError_t e;
     {
       KTimer kt(g, 6);
