@@ -221,10 +221,13 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   // Tickets are claimed in order by all P = grid x NP pipelines, so the tile
   // of ticket t + P is claimed about one tile period after t.  The claiming
   // thread (thread 32 of the pipeline, while thread 0 books the previous
-  // tile) prefetches that tile's input into L2 when its frame is already
-  // written, so the loads of the tile that follows hit in L2; then it checks
-  // FIR's firing rule on f0 for the claimed tile (bounded wait).
+  // tile) checks FIR's firing rule on f0 for the claimed tile (bounded
+  // wait) and, when the frame of tile t + P is already written, prefetches
+  // that tile's input into L2 during the look-back, so that its loads hit in
+  // L2.
   const unsigned long long P = static_cast<unsigned long long>(gridDim.x) * NP;
+  const float2 *pf_src = nullptr;  // thread 32: pending L2 prefetch
+  uint32_t pf_bytes = 0;
   auto claim = [&]() {
     const unsigned long long tk = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
     int rule = 0;
@@ -248,9 +251,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           const int64_t s0n = static_cast<int64_t>(tn) * kTTile;
           const int64_t lo = s0n >= static_cast<int64_t>(S) * kTR ? s0n - static_cast<int64_t>(S) * kTR : 0;
           const int64_t hi = min(s0n + static_cast<int64_t>(kTTile), f.L);
-          const float2 *src = f.src.frame(kn) + lo;
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(static_cast<uint32_t>((hi - lo) * 8))
-                       : "memory");
+          pf_src = f.src.frame(kn) + lo;  // issued later, while warps 1-3 idle in the look-back
+          pf_bytes = static_cast<uint32_t>((hi - lo) * 8);
         }
       }
     }
@@ -457,6 +459,9 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     if (warp == 0) {
       const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
       if (lane == 0) *s_prefix = pr;
+    } else if (tid == 32 && pf_bytes) {
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_src), "r"(pf_bytes) : "memory");
+      pf_bytes = 0;
     }
     psync();
     const long long prefix = *s_prefix;
