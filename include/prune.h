@@ -296,6 +296,33 @@ PRUNE_API prune_status prune_batch_pull(prune_batch *b, int32_t i, prune_frame_o
 /* Message of the last failure on b. */
 PRUNE_API const char *prune_batch_last_error(const prune_batch *b);
 
+/* Launch shape of a batch step.  The FIR launch has one CTA per (instance,
+ * tile of TS samples); the HX launch works through (instance, tile of rows)
+ * items of the selected blocks. */
+typedef struct prune_batch_tuning {
+  int32_t fir_order;  /* 0: FIR tiles instance by instance; 1: instances with more taps first */
+  int32_t hx_chunk;   /* 0: HX items spread over the grid by stride; > 0: each HX CTA fires this
+                         many consecutive items (an instance's H operands load once per CTA) */
+  int32_t hx_grid;    /* with hx_chunk = 0: CTAs of the HX launch (0: one wave) */
+  int32_t reserved;
+  double ms;          /* one step with this shape, as timed by prune_batch_autotune (else 0) */
+} prune_batch_tuning;
+
+/* Autotuner: fires the step on input x (as prune_batch_fire, without its
+ * CUDA graph) with every candidate launch shape, `reps` timed steps each
+ * (CUDA events on the batch's stream, after one untimed step), keeps the
+ * fastest and returns it in *best; all candidates with their times go to
+ * all[0..*n_all) (at most max_all; all may be NULL).  The candidates cross the
+ * two FIR orders with HX grid-stride over one wave and HX chunks of one, two
+ * and four waves.  The instances' state is left as it was: with the step
+ * parity unchanged every trial reads the same delay tokens and overwrites
+ * the same outputs.  Synchronous; cached step graphs are dropped. */
+PRUNE_API prune_status prune_batch_autotune(prune_batch *b, const void *x, int32_t reps, prune_batch_tuning *best,
+                                            prune_batch_tuning *all, int32_t max_all, int32_t *n_all);
+/* Set / read the launch shape in use (set drops cached step graphs). */
+PRUNE_API prune_status prune_batch_set_tuning(prune_batch *b, const prune_batch_tuning *t);
+PRUNE_API prune_status prune_batch_get_tuning(const prune_batch *b, prune_batch_tuning *t);
+
 /* ------------------------------------------------------------------------
  * Request loop (serving): streams of frames arrive and leave at run time.
  * Each admitted stream is one instance of the canonical graph whose

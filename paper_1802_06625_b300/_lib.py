@@ -28,6 +28,7 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_fire_frames_noalloc", "prune_batch_create", "prune_batch_destroy", "prune_batch_offset",
            "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error",
            "prune_hx_adjoint", "prune_fir_adjoint",
+           "prune_batch_autotune", "prune_batch_set_tuning", "prune_batch_get_tuning",
            "prune_server_create", "prune_server_destroy", "prune_server_open", "prune_server_submit",
            "prune_server_step", "prune_server_progress", "prune_server_poll", "prune_server_pull",
            "prune_server_close", "prune_server_sync", "prune_server_stats", "prune_server_last_error")
@@ -47,6 +48,11 @@ class prune_frame_out(ctypes.Structure):
 
 class prune_frame_view(ctypes.Structure):
     _fields_ = [("frame", I64), ("c", I32), ("reserved", I32), ("idx", P), ("y", P)]
+
+
+class prune_batch_tuning(ctypes.Structure):
+    _fields_ = [("fir_order", I32), ("hx_chunk", I32), ("hx_grid", I32), ("reserved", I32),
+                ("ms", ctypes.c_double)]
 
 
 class prune_server_desc(ctypes.Structure):
@@ -96,6 +102,10 @@ def load(path: str | None = None):
         "prune_batch_sync": [P],
         "prune_batch_pull": [P, I32, ctypes.POINTER(prune_frame_out), I32],
         "prune_hx_adjoint": [P, P, P, I32, I32, I32, I32, P, P, P, P, P],
+        "prune_batch_autotune": [P, P, I32, ctypes.POINTER(prune_batch_tuning), ctypes.POINTER(prune_batch_tuning),
+                                 I32, ctypes.POINTER(I32)],
+        "prune_batch_set_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
+        "prune_batch_get_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
         "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
         "prune_server_create": [ctypes.POINTER(prune_server_desc), ctypes.POINTER(P)],
         "prune_server_destroy": [P],

@@ -28,7 +28,9 @@ struct prune_batch {
   int32_t fir_tiles = 0, hx_items = 0;
   BatchInst *inst_d = nullptr;
   std::vector<BatchInst> inst_h;
-  int32_t *fir_map = nullptr, *hx_map = nullptr;
+  int2 *fir_map = nullptr;
+  int32_t *hx_map = nullptr;
+  prune_batch_tuning tuning{};  // launch shape in use (prune_batch_autotune)
   uint32_t *status = nullptr;
   int64_t steps = 0;
   // captured step graphs keyed by (input pointer, parity)
@@ -55,6 +57,23 @@ prune_status balloc(prune_batch *b, T **p, size_t count) {
   return PRUNE_OK;
 }
 
+// FIR CTAs in launch order: instance-major, or the tiles of the instances
+// with the most taps first (a tile costs about 8T flop per sample, so the
+// long tiles start first and the short ones fill the tail).
+std::vector<int2> fir_order(const prune_batch *b, int32_t order) {
+  std::vector<int32_t> inst(b->n);
+  for (int32_t i = 0; i < b->n; ++i) inst[i] = i;
+  if (order == 1)
+    std::stable_sort(inst.begin(), inst.end(), [&](int32_t a, int32_t c) { return b->T[a] > b->T[c]; });
+  std::vector<int2> m;
+  m.reserve(b->fir_tiles);
+  for (int32_t i : inst) {
+    const int64_t tiles = (b->F[i] * b->B + b->TS - 1) / b->TS;
+    for (int64_t t = 0; t < tiles; ++t) m.push_back(make_int2(i, static_cast<int32_t>(t)));
+  }
+  return m;
+}
+
 prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   BatchParams bp{};
   bp.inst = b->inst_d;
@@ -70,7 +89,8 @@ prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   bp.hx_items = b->hx_items;
   bp.timeout_ns = 2000000000ull;
   bp.status = b->status;
-  cudaError_t e = batch_launch_step(bp, b->tp_max, b->sms, b->stream);
+  bp.hx_chunk = b->tuning.hx_chunk;
+  cudaError_t e = batch_launch_step(bp, b->tp_max, b->sms, b->stream, b->tuning.hx_grid);
   if (e != cudaSuccess) return bfail(b, PRUNE_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return PRUNE_OK;
 }
@@ -138,7 +158,8 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
   }
   // layout: per-instance offsets in shared buffers
   int64_t samples = 0, taps_n = 0, hist_n = 0, blocks = 0;
-  std::vector<int32_t> fir_map, hx_map;
+  std::vector<int32_t> hx_map;
+  int64_t fir_count = 0;
   b->inst_h.resize(n);
   const int RB = N == kTcNc ? B / kTcNc : 0;
   for (int32_t i = 0; i < n; ++i) {
@@ -151,9 +172,8 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
     in.TP = fir_taps_padded(d.T);
     in.tau = d.tau;
     b->tp_max = std::max(b->tp_max, in.TP);
-    in.fir_tile0 = static_cast<int32_t>(fir_map.size());
-    const int64_t tiles = (L + b->TS - 1) / b->TS;
-    for (int64_t t = 0; t < tiles; ++t) fir_map.push_back(i);
+    in.fir_tile0 = static_cast<int32_t>(fir_count);
+    fir_count += (L + b->TS - 1) / b->TS;
     in.hx_tile0 = static_cast<int32_t>(hx_map.size());
     const int64_t items = N == kTcNc ? (static_cast<int64_t>(d.F) * RB + kTcM - 1) / kTcM : d.F;
     for (int64_t t = 0; t < items; ++t) hx_map.push_back(i);
@@ -166,7 +186,12 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
     blocks += d.F;
   }
   b->total_samples = samples;
-  b->fir_tiles = static_cast<int32_t>(fir_map.size());
+  if (fir_count > (int64_t{1} << 31) - 1) {
+    b->err = "prune_batch_create: too many FIR tiles";
+    return bail(PRUNE_EINVAL);
+  }
+  b->fir_tiles = static_cast<int32_t>(fir_count);
+  const std::vector<int2> fir_map = fir_order(b, 0);
   b->hx_items = static_cast<int32_t>(hx_map.size());
   float2 *taps = nullptr, *H = nullptr, *hist = nullptr, *y = nullptr, *outb = nullptr;
   float *energy = nullptr;
@@ -208,7 +233,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
        cudaMemsetAsync(b->status, 0, sizeof(uint32_t) * 4, b->stream) == cudaSuccess &&
        cudaMemcpyAsync(b->inst_d, b->inst_h.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream) ==
            cudaSuccess &&
-       cudaMemcpyAsync(b->fir_map, fir_map.data(), sizeof(int32_t) * fir_map.size(), cudaMemcpyHostToDevice,
+       cudaMemcpyAsync(b->fir_map, fir_map.data(), sizeof(int2) * fir_map.size(), cudaMemcpyHostToDevice,
                        b->stream) == cudaSuccess &&
        cudaMemcpyAsync(b->hx_map, hx_map.data(), sizeof(int32_t) * hx_map.size(), cudaMemcpyHostToDevice,
                        b->stream) == cudaSuccess;
@@ -299,5 +324,88 @@ prune_status prune_batch_pull(prune_batch *b, int32_t i, prune_frame_out *out, i
 }
 
 const char *prune_batch_last_error(const prune_batch *b) { return b ? b->err.c_str() : "NULL batch"; }
+
+prune_status prune_batch_set_tuning(prune_batch *b, const prune_batch_tuning *t) {
+  if (!b || !t || t->fir_order < 0 || t->fir_order > 1 || t->hx_chunk < 0 || t->hx_grid < 0)
+    return bfail(b, PRUNE_EINVAL, "prune_batch_set_tuning: bad arguments");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->dev);
+  prune_status s = PRUNE_OK;
+  if (t->fir_order != b->tuning.fir_order) {
+    const std::vector<int2> m = fir_order(b, t->fir_order);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+        cudaMemcpy(b->fir_map, m.data(), sizeof(int2) * m.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      s = bfail(b, PRUNE_ECUDA, "prune_batch_set_tuning: map upload failed");
+  }
+  if (s == PRUNE_OK) {
+    b->tuning = *t;
+    for (auto &c : b->graphs) cudaGraphExecDestroy(c.exec);
+    b->graphs.clear();
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return s;
+}
+
+prune_status prune_batch_get_tuning(const prune_batch *b, prune_batch_tuning *t) {
+  if (!b || !t) return bfail(nullptr, PRUNE_EINVAL, "prune_batch_get_tuning: NULL argument");
+  *t = b->tuning;
+  return PRUNE_OK;
+}
+
+prune_status prune_batch_autotune(prune_batch *b, const void *x, int32_t reps, prune_batch_tuning *best,
+                                  prune_batch_tuning *all, int32_t max_all, int32_t *n_all) {
+  if (n_all) *n_all = 0;
+  if (!b || !x || !best || reps < 1 || max_all < 0 || (max_all > 0 && !all))
+    return bfail(b, PRUNE_EINVAL, "prune_batch_autotune: bad arguments");
+  if (reinterpret_cast<uintptr_t>(x) & 15u) return bfail(b, PRUNE_EINVAL, "prune_batch_autotune: x must be 16-byte aligned");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->dev);
+  const int parity = static_cast<int>(b->steps & 1);
+  const int wave = b->N == kTcNc ? b->sms : 8 * b->sms;
+  std::vector<prune_batch_tuning> cand;
+  for (int32_t order = 0; order < 2; ++order) {
+    cand.push_back(prune_batch_tuning{order, 0, wave, 0, 0.0});
+    for (int waves : {1, 2, 4}) {
+      const int32_t chunk = std::max(1, (b->hx_items + waves * wave - 1) / (waves * wave));
+      cand.push_back(prune_batch_tuning{order, chunk, 0, 0, 0.0});
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  prune_status s = PRUNE_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    s = bfail(b, PRUNE_ECUDA, "prune_batch_autotune: event creation failed");
+  int besti = -1;
+  for (size_t i = 0; i < cand.size() && s == PRUNE_OK; ++i) {
+    s = prune_batch_set_tuning(b, &cand[i]);
+    if (s == PRUNE_OK) s = enqueue_step(b, static_cast<const float2 *>(x), parity);  // untimed
+    if (s != PRUNE_OK) break;
+    cudaEventRecord(e0, b->stream);
+    for (int32_t r = 0; r < reps && s == PRUNE_OK; ++r) s = enqueue_step(b, static_cast<const float2 *>(x), parity);
+    cudaEventRecord(e1, b->stream);
+    if (s != PRUNE_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      s = bfail(b, PRUNE_ECUDA, "prune_batch_autotune: timing failed");
+      break;
+    }
+    cand[i].ms = ms / reps;
+    if (besti < 0 || cand[i].ms < cand[besti].ms) besti = static_cast<int>(i);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s == PRUNE_OK) s = prune_batch_sync(b);
+  if (s == PRUNE_OK) s = prune_batch_set_tuning(b, &cand[besti]);
+  if (s == PRUNE_OK) {
+    b->tuning.ms = cand[besti].ms;
+    *best = cand[besti];
+    const int32_t k = std::min<int32_t>(max_all, static_cast<int32_t>(cand.size()));
+    for (int32_t i = 0; i < k; ++i) all[i] = cand[i];
+    if (n_all) *n_all = k;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return s;
+}
 
 }  // extern "C"

@@ -32,10 +32,11 @@ struct BatchInst {
 
 struct BatchParams {
   const BatchInst *inst;
-  const int32_t *fir_map;   // FIR tile -> instance
-  const int32_t *hx_map;    // HX work item -> instance
+  const int2 *fir_map;      // FIR CTA -> (instance, tile of the instance), in launch order
+  const int32_t *hx_map;    // HX work item -> instance (an instance's items are consecutive)
   const float2 *x;          // step input, all instances back to back
   int32_t n, B, N, TS, parity, fir_tiles, hx_items;
+  int32_t hx_chunk;         // > 0: CTA c fires items [c * hx_chunk, (c + 1) * hx_chunk); 0: grid-stride
   uint64_t timeout_ns;
   uint32_t *status;
 };
@@ -44,8 +45,8 @@ struct BatchParams {
 // the single-instance kernel, so both paths compute identical energies.
 static __global__ void __launch_bounds__(kFirThreads) batch_fir_kernel(BatchParams bp, int32_t tp_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int gt = blockIdx.x;
-  const int ii = bp.fir_map[gt];
+  const int2 tm = bp.fir_map[blockIdx.x];
+  const int ii = tm.x;
   const BatchInst in = bp.inst[ii];
   const int TP = in.TP;
   float2 *xs = reinterpret_cast<float2 *>(smem_raw);
@@ -54,7 +55,7 @@ static __global__ void __launch_bounds__(kFirThreads) batch_fir_kernel(BatchPara
   float *Et = red + 32;
   const int tid = threadIdx.x;
   const int64_t L = static_cast<int64_t>(in.F) * bp.B;
-  const int64_t s0 = static_cast<int64_t>(gt - in.fir_tile0) * bp.TS;
+  const int64_t s0 = static_cast<int64_t>(tm.y) * bp.TS;
   const int nv = static_cast<int>(min(static_cast<int64_t>(bp.TS), L - s0));
   const float2 *cur = in.x ? in.x : bp.x + in.x_off;
   const float2 *hist = in.T <= 1 ? nullptr : in.hist ? in.hist + bp.parity * (in.T - 1) : in.hist_in;
@@ -122,7 +123,10 @@ static __global__ void __launch_bounds__(kHxThreads) batch_hx_cuda_kernel(BatchP
   float2 *hs = xs + bp.B;
   const int tid = threadIdx.x, N = bp.N;
   int loaded = -1;
-  for (int w = blockIdx.x; w < bp.hx_items; w += gridDim.x) {
+  const int w0 = bp.hx_chunk > 0 ? blockIdx.x * bp.hx_chunk : blockIdx.x;
+  const int w1 = bp.hx_chunk > 0 ? min(w0 + bp.hx_chunk, bp.hx_items) : bp.hx_items;
+  const int ws = bp.hx_chunk > 0 ? 1 : gridDim.x;
+  for (int w = w0; w < w1; w += ws) {
     const int ii = bp.hx_map[w];
     const BatchInst &in = bp.inst[ii];
     const int j = w - in.hx_tile0;
@@ -181,7 +185,10 @@ static __global__ void __launch_bounds__(kTcThreads, 1) batch_hx_tc_kernel(Batch
   uint32_t phase = 0;
   bool pending = false;
   int loaded = -1;
-  for (int w = blockIdx.x; w < bp.hx_items; w += gridDim.x) {
+  const int w0 = bp.hx_chunk > 0 ? blockIdx.x * bp.hx_chunk : blockIdx.x;
+  const int w1 = bp.hx_chunk > 0 ? min(w0 + bp.hx_chunk, bp.hx_items) : bp.hx_items;
+  const int ws = bp.hx_chunk > 0 ? 1 : gridDim.x;
+  for (int w = w0; w < w1; w += ws) {
     const int ii = bp.hx_map[w];
     const BatchInst &in = bp.inst[ii];
     const int tau = w - in.hx_tile0;
@@ -280,14 +287,19 @@ static __global__ void __launch_bounds__(kTcThreads, 1) batch_hx_tc_kernel(Batch
 // the request loop share them).  Dynamic shared memory above 48 KB must have
 // been enabled on these kernels in the calling translation unit
 // (batch_enable_smem).
-static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, int sms, cudaStream_t stream) {
+// hx_grid: CTAs of the HX launch (0: one wave, sms for tensor cores, 8 sms
+// for CUDA cores); with bp.hx_chunk > 0 the grid covers the items in chunks.
+static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, int sms, cudaStream_t stream,
+                                            int hx_grid = 0) {
   batch_fir_kernel<<<bp.fir_tiles, kFirThreads, fir_smem_bytes(tp_max), stream>>>(bp, tp_max);
   batch_detsel_kernel<<<bp.n, kDetThreads, 0, stream>>>(bp);
+  const int wave = bp.N == kTcNc ? sms : sms * 8;
+  const int want = bp.hx_chunk > 0 ? (bp.hx_items + bp.hx_chunk - 1) / bp.hx_chunk : (hx_grid > 0 ? hx_grid : wave);
   if (bp.N == kTcNc) {
-    const int grid = std::max(1, std::min(bp.hx_items, sms));
+    const int grid = std::max(1, std::min(bp.hx_items, want));
     batch_hx_tc_kernel<<<grid, kTcThreads, kTcSmemBytes, stream>>>(bp);
   } else {
-    const int grid = std::max(1, std::min(bp.hx_items, sms * 8));
+    const int grid = std::max(1, std::min(bp.hx_items, want));
     const size_t smem = (static_cast<size_t>(bp.B) + static_cast<size_t>(bp.N) * bp.N) * sizeof(float2);
     batch_hx_cuda_kernel<<<grid, kHxThreads, smem, stream>>>(bp);
   }

@@ -39,7 +39,8 @@ struct prune_server {
   // staging of the step tables, one set per step in flight
   struct Stage {
     BatchInst *inst_h = nullptr, *inst_d = nullptr;
-    int32_t *fir_h = nullptr, *fir_d = nullptr, *hx_h = nullptr, *hx_d = nullptr;
+    int2 *fir_h = nullptr, *fir_d = nullptr;
+    int32_t *hx_h = nullptr, *hx_d = nullptr;
     cudaEvent_t ev = nullptr;
   };
   std::vector<Stage> stage;
@@ -221,10 +222,10 @@ prune_status prune_server_create(const prune_server_desc *d, prune_server **out)
   s->stage.resize(d->max_inflight);
   for (auto &t : s->stage) {
     if (cudaHostAlloc(reinterpret_cast<void **>(&t.inst_h), sizeof(BatchInst) * s->max_entries, 0) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void **>(&t.fir_h), sizeof(int32_t) * s->max_fir, 0) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&t.fir_h), sizeof(int2) * s->max_fir, 0) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void **>(&t.hx_h), sizeof(int32_t) * s->max_hx, 0) != cudaSuccess ||
         cudaMalloc(&t.inst_d, sizeof(BatchInst) * s->max_entries) != cudaSuccess ||
-        cudaMalloc(&t.fir_d, sizeof(int32_t) * s->max_fir) != cudaSuccess ||
+        cudaMalloc(&t.fir_d, sizeof(int2) * s->max_fir) != cudaSuccess ||
         cudaMalloc(&t.hx_d, sizeof(int32_t) * s->max_hx) != cudaSuccess ||
         cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(PRUNE_ENOMEM, "prune_server_create: step staging");
@@ -356,7 +357,7 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
     in.fir_tile0 = nfir;
     in.hx_tile0 = nhx;
     const int64_t tiles = (L + s->TS - 1) / s->TS, items = hx_items_of(ss.F, B, N);
-    for (int64_t q = 0; q < tiles; ++q) t.fir_h[nfir++] = static_cast<int32_t>(e);
+    for (int64_t q = 0; q < tiles; ++q) t.fir_h[nfir++] = make_int2(static_cast<int32_t>(e), static_cast<int32_t>(q));
     for (int64_t q = 0; q < items; ++q) t.hx_h[nhx++] = static_cast<int32_t>(e);
     t.inst_h[e] = in;
     if (p.last && ss.T > 1) ss.parity ^= 1;
@@ -380,7 +381,7 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
   bp.status = s->status;
   bool ok = cudaMemcpyAsync(t.inst_d, t.inst_h, sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s->stream) ==
                 cudaSuccess &&
-            cudaMemcpyAsync(t.fir_d, t.fir_h, sizeof(int32_t) * nfir, cudaMemcpyHostToDevice, s->stream) ==
+            cudaMemcpyAsync(t.fir_d, t.fir_h, sizeof(int2) * nfir, cudaMemcpyHostToDevice, s->stream) ==
                 cudaSuccess &&
             cudaMemcpyAsync(t.hx_d, t.hx_h, sizeof(int32_t) * nhx, cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
   cudaError_t e = ok ? batch_launch_step(bp, s->tp_max, s->sms, s->stream) : cudaGetLastError();

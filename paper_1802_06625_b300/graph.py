@@ -232,6 +232,30 @@ class Batch:
     def sync(self):
         check(_lib.lib().prune_batch_sync(self.h), batch=self.h)
 
+    @staticmethod
+    def _tuning_dict(t):
+        return {"fir_order": t.fir_order, "hx_chunk": t.hx_chunk, "hx_grid": t.hx_grid, "ms": t.ms}
+
+    def autotune(self, x, reps=3):
+        """Time every candidate launch shape on one step of x and keep the
+        fastest; returns (best, all candidates) as dicts."""
+        assert x.is_cuda and x.numel() == self.total
+        best = _lib.prune_batch_tuning()
+        allc = (_lib.prune_batch_tuning * 16)()
+        n = ctypes.c_int32()
+        check(_lib.lib().prune_batch_autotune(self.h, x.data_ptr(), reps, ctypes.byref(best), allc, 16,
+                                              ctypes.byref(n)), batch=self.h)
+        return self._tuning_dict(best), [self._tuning_dict(allc[i]) for i in range(n.value)]
+
+    def set_tuning(self, fir_order=0, hx_chunk=0, hx_grid=0):
+        t = _lib.prune_batch_tuning(fir_order=fir_order, hx_chunk=hx_chunk, hx_grid=hx_grid)
+        check(_lib.lib().prune_batch_set_tuning(self.h, ctypes.byref(t)), batch=self.h)
+
+    def tuning(self):
+        t = _lib.prune_batch_tuning()
+        check(_lib.lib().prune_batch_get_tuning(self.h, ctypes.byref(t)), batch=self.h)
+        return self._tuning_dict(t)
+
     def pull(self, i):
         F = self.F[i]
         idx = np.zeros(F, np.int32)

@@ -99,3 +99,46 @@ def test_batched_workload_shapes_fire(G):
         if rms > 0:
             assert err <= TOL_REL * rms
     bt.close()
+
+
+@pytest.mark.parametrize("N", [64, 16])
+def test_every_launch_shape_gives_identical_results_and_autotune_keeps_state(G, N):
+    # the launch shape changes only which CTA fires which tile: results are
+    # bit-identical; autotuning fires the step repeatedly at the same parity,
+    # so the instances' delay tokens and step count are untouched
+    B = 256
+    ws = _instances(B, N, seed=41 + N, n=7)
+    insts = [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws]
+    frames = [[w.frame(k) for w in ws] for k in range(2)]
+    xs = [torch.cat([f.reshape(-1) for f in frames[k]]).cuda() for k in range(2)]
+    ref = G.Batch(B, N, insts)
+    recs_ref = []
+    for k in range(2):
+        ref.fire(xs[k])
+        ref.sync()
+        recs_ref.append([ref.pull(i) for i in range(len(ws))])
+    ref.close()
+    shapes = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 3, 0), (0, 0, 1), (1, 0, 7)]
+    for fo, ch, gr in shapes:
+        bt = G.Batch(B, N, insts)
+        bt.set_tuning(fir_order=fo, hx_chunk=ch, hx_grid=gr)
+        assert bt.tuning()["hx_chunk"] == ch
+        for k in range(2):
+            bt.fire(xs[k], graph=(k == 1))
+            bt.sync()
+            for i in range(len(ws)):
+                a, r = bt.pull(i), recs_ref[k][i]
+                assert a[0] == r[0] and a[1] == r[1]
+                assert np.array_equal(a[2], r[2]) and np.array_equal(a[3], r[3]), (fo, ch, gr, k, i)
+        bt.close()
+    at = G.Batch(B, N, insts)
+    best, allc = at.autotune(xs[0], reps=2)
+    assert len(allc) == 8 and all(c["ms"] > 0 for c in allc)
+    assert best["ms"] == min(c["ms"] for c in allc) and at.tuning()["ms"] == best["ms"]
+    for k in range(2):
+        at.fire(xs[k], graph=True)
+        at.sync()
+        for i in range(len(ws)):
+            a, r = at.pull(i), recs_ref[k][i]
+            assert a[0] == r[0] and np.array_equal(a[2], r[2]) and np.array_equal(a[3], r[3])
+    at.close()
