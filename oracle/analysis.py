@@ -569,6 +569,50 @@ def canonical_graph(F, swap_sink_elements=None, delay_f4=0, delay_f5=0):
     return g
 
 
+def dpd_graph(K=10):
+    """The Dynamic Predistortion graph of Sec. VII-A2 (figure missing from the
+    source; rebuilt from the prose): SRC emits one period of input samples to
+    the polynomial actor POLY and one external configuration token to the
+    configuration actor CONF; CONF's control value selects which of the K
+    branches fire in the period.  POLY (dynamic, output DRPs) feeds branch k
+    to FIR_k (static, with a self-loop delay token: the filter's history), and
+    the adder ADD (dynamic, input DRPs) sums the branches that fired into SINK.
+    Token unit: one period of samples.  The DPG is (CONF, POLY, ADD) with K
+    DCs {FIR_k}."""
+    g = Graph()
+    for a, k in (("SRC", STATIC), ("CONF", CONFIG), ("POLY", DYNAMIC), ("ADD", DYNAMIC), ("SINK", STATIC)):
+        g.add_actor(a, k)
+    g.add_port("SRC", "x", True, SRP, 1)
+    g.add_port("SRC", "cfg", True, SRP, 1)
+    g.add_port("CONF", "in", False, SRP, 1)
+    g.add_port("CONF", "ctl", True, CTRL_OUT, 1)
+    g.add_port("POLY", "c", False, CTRL_IN, 1)
+    g.add_port("POLY", "in", False, SRP, 1)
+    g.add_port("ADD", "c", False, CTRL_IN, 1)
+    g.add_port("ADD", "out", True, SRP, 1)
+    g.add_port("SINK", "in", False, SRP, 1)
+    g.connect("fx", ("SRC", "x"), ("POLY", "in"), 1)
+    g.connect("fcfg", ("SRC", "cfg"), ("CONF", "in"), 1)
+    g.connect("fcp", ("CONF", "ctl"), ("POLY", "c"), 1)
+    g.connect("fca", ("CONF", "ctl"), ("ADD", "c"), 1)
+    g.connect("fy", ("ADD", "out"), ("SINK", "in"), 1)
+    for k in range(K):
+        fir = f"FIR_{k}"
+        g.add_actor(fir, STATIC)
+        g.add_port("POLY", f"o{k}", True, DRP, 1)
+        g.add_port(fir, "in", False, SRP, 1)
+        g.add_port(fir, "hin", False, SRP, 1)
+        g.add_port(fir, "hout", True, SRP, 1)
+        g.add_port(fir, "out", True, SRP, 1)
+        g.add_port("ADD", f"i{k}", False, DRP, 1)
+        g.connect(f"fp_{k}", ("POLY", f"o{k}"), (fir, "in"), 1)
+        g.connect(f"fh_{k}", (fir, "hout"), (fir, "hin"), 1, delay=1)
+        g.connect(f"ff_{k}", (fir, "out"), ("ADD", f"i{k}"), 1)
+        g.table[(("CONF", "ctl"), ("POLY", f"o{k}"))] = k + 1
+        g.table[(("CONF", "ctl"), ("ADD", f"i{k}"))] = k + 1
+    return g
+
+
 # ---------------------------------------------------------------------------
 # Brute-force deadlock / boundedness search (token counts and control values)
 # ---------------------------------------------------------------------------
