@@ -312,6 +312,10 @@ def run_ours(args, w):
     if not args.no_batched and ws == 1:
         line["batched"] = run_batched(args, dev)
 
+    # the Dynamic Predistortion stream
+    if not args.no_dpd and ws == 1:
+        line["dpd"] = run_dpd(args, dev)
+
     # the request loop: Poisson stream arrivals, admission by HBM budget
     if not args.no_serving and ws == 1:
         line["serving"] = run_serving(args, dev)
@@ -384,6 +388,40 @@ def run_batched(args, dev):
             "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
                       "graph with the autotuned launch shape, plain = one graph object per instance (push, run, "
                       "drop per step)"}
+
+
+def run_dpd(args, dev):
+    """The 67 M-sample DPD stream (1024 periods of 65536 samples, 10 branches
+    of 10 taps, 2..10 active per period) fired in one call per step, the
+    delay tokens carried in place; CUDA events on the current stream."""
+    from paper_1802_06625_b300 import dpd
+
+    w = synth.DPD
+    masks = w.masks()
+    taps = w.taps()
+    x = w.x(device=dev)
+    y = torch.empty_like(x)
+    h = torch.zeros(w.K, w.T - 1, dtype=torch.complex64, device=dev)
+    for _ in range(args.warmup):
+        dpd.fire(x, masks, taps, w.period, hist=h, hist_out=h, y=y)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        dpd.fire(x, masks, taps, w.period, hist=h, hist_out=h, y=y)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    active = sum(bin(int(m)).count("1") for m in masks)
+    flops = active * w.period * 8.0 * w.T               # complex MACs of the active branches
+    samples = w.periods * w.period
+    return {"workload": w.name, "samples_per_step": samples, "Msamples_s": samples / (ms * 1e-3) / 1e6,
+            "ms_per_step": ms, "mean_active_branches": active / w.periods,
+            "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2.032 GHz",
+                         "hbm_GBs": 16.0 * samples / (ms * 1e-3) / 1e9},
+            "paper": "PRUNE heterogeneous 106 Msamples/s on the RX platform (Table 4), other hardware: context only"}
 
 
 def run_serving(args, dev):
@@ -533,6 +571,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--no-dpd", action="store_true", help="skip the DPD stream measurement")
     ap.add_argument("--serve-streams", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")

@@ -411,6 +411,39 @@ PRUNE_API prune_status prune_server_stats(prune_server *s, uint64_t *hbm_used, u
 PRUNE_API const char *prune_server_last_error(const prune_server *s);
 
 /* ------------------------------------------------------------------------
+ * Dynamic Predistortion workload (Sec. VII-A2): a polynomial actor feeds K
+ * parallel T-tap complex FIR filters (the DCs of a DPG), a configuration
+ * actor selects from an external input, once per period, which filters fire,
+ * and an adder sums them.  Branch k = 1..K carries psi_k(x) = x |x|^(k-1).
+ * A filter that does not fire keeps its delay token (its last T-1 inputs)
+ * until it fires again.  For every sample n of period p:
+ *   y[n] = sum over k with bit k-1 of mask[p] set of sum_{t<T} h_k[t] psi_k[n-t]
+ * where psi_k[n-t] before the period's first sample comes from branch k's
+ * delay token.  All periods fire in parallel (a scan over the masks gives
+ * every period its branches' tokens).
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace prune_dpd_fire needs for P periods, K branches. */
+PRUNE_API size_t prune_dpd_workspace_bytes(int32_t P, int32_t K);
+
+/* Fire P periods of `period` samples (period a multiple of 8, >= T-1).
+ *   x        device, [P][period] complex64, 16-byte aligned
+ *   mask     device, [P] uint16: bit k-1 set = branch k fires in that period
+ *            (bits >= K ignored; 0 = no branch: y is zero there)
+ *   taps     device, [K][T] complex64, h_k[t] at taps[(k-1)*T + t]
+ *   hist_in  device, [K][T-1] complex64 delay tokens before period 0, or NULL
+ *            (zeros)
+ *   hist_out device, [K][T-1] tokens after the last period, or NULL; may alias
+ *            hist_in
+ *   y        device, [P][period] complex64, 16-byte aligned
+ *   workspace device, prune_dpd_workspace_bytes(P, K) bytes, caller-owned
+ * 1 <= K <= 16, 1 <= T <= 16, P <= 65535.  Asynchronous on `stream`;
+ * PRUNE_EINVAL (message in prune_last_error(NULL)) enqueues nothing. */
+PRUNE_API prune_status prune_dpd_fire(const void *x, int64_t period, int32_t P, const uint16_t *mask, int32_t K,
+                                      int32_t T, const void *taps, const void *hist_in, void *hist_out, void *y,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Adjoints over a recorded control trace (training the taps and H).  The
  * decisions v[b] = E_b > tau are piecewise constant in the parameters, so
  * with the trace (c, idx) of a forward firing held fixed the sink output is

@@ -29,6 +29,7 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_batch_fire", "prune_batch_sync", "prune_batch_pull", "prune_batch_last_error",
            "prune_hx_adjoint", "prune_fir_adjoint",
            "prune_batch_autotune", "prune_batch_set_tuning", "prune_batch_get_tuning",
+           "prune_dpd_workspace_bytes", "prune_dpd_fire",
            "prune_server_create", "prune_server_destroy", "prune_server_open", "prune_server_submit",
            "prune_server_step", "prune_server_progress", "prune_server_poll", "prune_server_pull",
            "prune_server_close", "prune_server_sync", "prune_server_stats", "prune_server_last_error")
@@ -105,6 +106,7 @@ def load(path: str | None = None):
         "prune_batch_autotune": [P, P, I32, ctypes.POINTER(prune_batch_tuning), ctypes.POINTER(prune_batch_tuning),
                                  I32, ctypes.POINTER(I32)],
         "prune_batch_set_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
+        "prune_dpd_fire": [P, I64, I32, P, I32, I32, P, P, P, P, P, ctypes.c_size_t, P],
         "prune_batch_get_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
         "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
         "prune_server_create": [ctypes.POINTER(prune_server_desc), ctypes.POINTER(P)],
@@ -129,6 +131,8 @@ def load(path: str | None = None):
     lib.prune_last_error.restype = ctypes.c_char_p
     lib.prune_batch_last_error.argtypes = [P]
     lib.prune_batch_last_error.restype = ctypes.c_char_p
+    lib.prune_dpd_workspace_bytes.argtypes = [I32, I32]
+    lib.prune_dpd_workspace_bytes.restype = ctypes.c_size_t
     lib.prune_server_last_error.argtypes = [P]
     lib.prune_server_last_error.restype = ctypes.c_char_p
     return lib

@@ -30,7 +30,7 @@ GOLDEN = 0x9E3779B97F4A7C15
 _C1 = 0xBF58476D1CE4E5B9
 _C2 = 0x94D049BB133111EB
 
-TAG_X, TAG_TAPS, TAG_H, TAG_BURST, TAG_FRAC, TAG_TAU, TAG_SHAPE, TAG_ARRIVAL = 1, 2, 3, 4, 5, 6, 7, 8
+TAG_X, TAG_TAPS, TAG_H, TAG_BURST, TAG_FRAC, TAG_TAU, TAG_SHAPE, TAG_ARRIVAL, TAG_MASK = 1, 2, 3, 4, 5, 6, 7, 8, 9
 
 
 def mix64(z: int) -> int:
@@ -282,3 +282,43 @@ class ServingWorkload:
 # Streams arriving at 2000/s, 10..10^4 frames each, F in [64, 2048],
 # B = 512, T = 32, H 64x64 per stream.
 SERVING = ServingWorkload("serving_poisson2000_B512_T32_N64", streams=256, lam=2000.0, B=512, T=32, N=64, seed=5)
+
+
+@dataclass
+class DpdWorkload:
+    """The Dynamic Predistortion stream: P periods of `period` samples of
+    CN(0, var) input, K branches of T taps ~ CN(0, 1/(K T)) each, and per
+    period an active set of a ~ U{a_lo..a_hi} branches drawn without
+    replacement (the external configuration input)."""
+    name: str
+    periods: int
+    period: int
+    K: int
+    T: int
+    seed: int
+    var: float = 0.25
+    a_lo: int = 2
+    a_hi: int = 10
+
+    def x(self, p0: int = 0, n: int | None = None, device="cpu") -> torch.Tensor:
+        n = self.periods - p0 if n is None else n
+        return cnormal(stream_key(self.seed, TAG_X), n * self.period, self.var, device,
+                       start=p0 * self.period).to(torch.complex64)
+
+    def taps(self, device="cpu") -> torch.Tensor:
+        return cnormal(stream_key(self.seed, TAG_TAPS), self.K * self.T, 1.0 / (self.K * self.T),
+                       device).to(torch.complex64).view(self.K, self.T)
+
+    def masks(self) -> torch.Tensor:
+        out = []
+        for p in range(self.periods):
+            u = uniform(stream_key(self.seed, TAG_MASK, p), 0, 1 + self.K)
+            a = self.a_lo + min(int(float(u[0]) * (self.a_hi - self.a_lo + 1)), self.a_hi - self.a_lo)
+            order = torch.argsort(u[1:], stable=True)[:a]
+            out.append(int(sum(1 << int(k) for k in order)))
+        return torch.tensor(out, dtype=torch.int32)
+
+
+# 67 M samples (1024 periods of 65536) as in the paper's DPD stream, 10
+# branches of 10 taps, 2..10 branches active per period.
+DPD = DpdWorkload("dpd_1024x65536_K10_T10", periods=1024, period=65536, K=10, T=10, seed=6)
