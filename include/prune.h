@@ -411,6 +411,66 @@ PRUNE_API prune_status prune_server_stats(prune_server *s, uint64_t *hbm_used, u
 PRUNE_API const char *prune_server_last_error(const prune_server *s);
 
 /* ------------------------------------------------------------------------
+ * Graph front end: a PRUNE graph described actor by actor, port by port and
+ * FIFO by FIFO (Sec. III), checked by the compile-time analysis of Sec. IV-V
+ * and matched against the forms this runtime fires.  Host only; no device
+ * needed.  A model is used by one host thread at a time.
+ * ---------------------------------------------------------------------- */
+
+typedef struct prune_model prune_model;
+
+enum { PRUNE_ACTOR_STATIC = 0, PRUNE_ACTOR_DYNAMIC = 1, PRUNE_ACTOR_CONFIG = 2 };
+enum { PRUNE_PORT_SRP = 0, PRUNE_PORT_DRP = 1, PRUNE_PORT_CTRL_IN = 2, PRUNE_PORT_CTRL_OUT = 3 };
+enum {
+  PRUNE_FORM_NONE = 0,      /* not a form the runtime fires */
+  PRUNE_FORM_CANONICAL = 1, /* one DPG whose DCs are single static actors without delay
+                               (HX_b): prune_graph_create with F = units */
+  PRUNE_FORM_DPD = 2        /* one DPG whose DCs are single static actors each with a
+                               self-loop delay (FIR_k): prune_dpd_fire with K = units */
+};
+
+typedef struct prune_model_report {
+  int32_t rate_errors;    /* Sec. III-A: port atr != fiforate, control rate != 1, or a
+                             port connected against its direction */
+  int32_t type_errors;    /* Sec. III-B: ports an actor's type does not allow */
+  int32_t rule_errors[5]; /* violations of design rules 1..5 (Sec. IV) */
+  int32_t n_dpgs;         /* DPGs found: (q, x, y) with x's output DRPs and y's input
+                             DRPs controlled by one control output port of q */
+  int32_t consistent;     /* every DPG valid and consistent (Sec. V theorem) */
+  char first_error[256];  /* the first violation found, or empty */
+} prune_model_report;
+
+PRUNE_API prune_status prune_model_create(prune_model **out);
+PRUNE_API prune_status prune_model_destroy(prune_model *m);
+/* Actors, ports and FIFOs get dense ids from 0 in creation order.  atr is
+ * the port's active token rate (the itr of a DRP is 0, eq. (1)); control
+ * ports have rate 1.  A FIFO runs from an output port to an input port with
+ * `rate` tokens per firing and `delay` initial tokens. */
+PRUNE_API prune_status prune_model_add_actor(prune_model *m, const char *name, int32_t kind, int32_t *actor);
+PRUNE_API prune_status prune_model_add_port(prune_model *m, int32_t actor, const char *name, int32_t is_output,
+                                            int32_t kind, int64_t atr, int32_t *port);
+PRUNE_API prune_status prune_model_connect(prune_model *m, int32_t src_port, int32_t dst_port, int64_t rate,
+                                           int64_t delay, int32_t *fifo);
+/* Control table T[ctrl_out][drp] = element (1-based element of the control
+ * token; 0 = not controlled). */
+PRUNE_API prune_status prune_model_set_control(prune_model *m, int32_t ctrl_out_port, int32_t drp, int32_t element);
+/* Run the analysis (cached until the model changes) and report. */
+PRUNE_API prune_status prune_model_check(prune_model *m, prune_model_report *rep);
+/* DPG i: its actors, number of DCs, validity and consistency. */
+PRUNE_API prune_status prune_model_dpg(prune_model *m, int32_t i, int32_t *q, int32_t *x, int32_t *y,
+                                       int32_t *n_dcs, int32_t *valid, int32_t *consistent);
+/* DC k of DPG i: its members (actor ids; a dummy actor of the DC procedure's
+ * step 1 is -(fifo + 1)) and its control element (0 if not unique). */
+PRUNE_API prune_status prune_model_dc(prune_model *m, int32_t i, int32_t k, int32_t *members, int32_t max,
+                                      int32_t *n, int32_t *element);
+/* beta(f): the maximum over the DCs of the tokens on FIFO f during one period
+ * of the DC's schedule (0 for FIFOs outside every DC; Sec. V proof). */
+PRUNE_API prune_status prune_model_buffer_bound(prune_model *m, int32_t fifo, int64_t *beta);
+/* Which runtime form the model is (PRUNE_FORM_*) and its number of DCs. */
+PRUNE_API prune_status prune_model_classify(prune_model *m, int32_t *form, int32_t *units);
+PRUNE_API const char *prune_model_last_error(const prune_model *m);
+
+/* ------------------------------------------------------------------------
  * Dynamic Predistortion workload (Sec. VII-A2): a polynomial actor feeds K
  * parallel T-tap complex FIR filters (the DCs of a DPG), a configuration
  * actor selects from an external input, once per period, which filters fire,

@@ -30,6 +30,9 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_hx_adjoint", "prune_fir_adjoint",
            "prune_batch_autotune", "prune_batch_set_tuning", "prune_batch_get_tuning",
            "prune_dpd_workspace_bytes", "prune_dpd_fire",
+           "prune_model_create", "prune_model_destroy", "prune_model_add_actor", "prune_model_add_port",
+           "prune_model_connect", "prune_model_set_control", "prune_model_check", "prune_model_dpg",
+           "prune_model_dc", "prune_model_buffer_bound", "prune_model_classify", "prune_model_last_error",
            "prune_server_create", "prune_server_destroy", "prune_server_open", "prune_server_submit",
            "prune_server_step", "prune_server_progress", "prune_server_poll", "prune_server_pull",
            "prune_server_close", "prune_server_sync", "prune_server_stats", "prune_server_last_error")
@@ -54,6 +57,11 @@ class prune_frame_view(ctypes.Structure):
 class prune_batch_tuning(ctypes.Structure):
     _fields_ = [("fir_order", I32), ("hx_chunk", I32), ("hx_grid", I32), ("reserved", I32),
                 ("ms", ctypes.c_double)]
+
+
+class prune_model_report(ctypes.Structure):
+    _fields_ = [("rate_errors", I32), ("type_errors", I32), ("rule_errors", I32 * 5), ("n_dpgs", I32),
+                ("consistent", I32), ("first_error", ctypes.c_char * 256)]
 
 
 class prune_server_desc(ctypes.Structure):
@@ -107,6 +115,17 @@ def load(path: str | None = None):
                                  I32, ctypes.POINTER(I32)],
         "prune_batch_set_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
         "prune_dpd_fire": [P, I64, I32, P, I32, I32, P, P, P, P, P, ctypes.c_size_t, P],
+        "prune_model_create": [ctypes.POINTER(P)],
+        "prune_model_destroy": [P],
+        "prune_model_add_actor": [P, ctypes.c_char_p, I32, ctypes.POINTER(I32)],
+        "prune_model_add_port": [P, I32, ctypes.c_char_p, I32, I32, I64, ctypes.POINTER(I32)],
+        "prune_model_connect": [P, I32, I32, I64, I64, ctypes.POINTER(I32)],
+        "prune_model_set_control": [P, I32, I32, I32],
+        "prune_model_check": [P, ctypes.POINTER(prune_model_report)],
+        "prune_model_dpg": [P, I32] + [ctypes.POINTER(I32)] * 6,
+        "prune_model_dc": [P, I32, I32, ctypes.POINTER(I32), I32, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "prune_model_buffer_bound": [P, I32, ctypes.POINTER(I64)],
+        "prune_model_classify": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "prune_batch_get_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
         "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
         "prune_server_create": [ctypes.POINTER(prune_server_desc), ctypes.POINTER(P)],
@@ -133,6 +152,8 @@ def load(path: str | None = None):
     lib.prune_batch_last_error.restype = ctypes.c_char_p
     lib.prune_dpd_workspace_bytes.argtypes = [I32, I32]
     lib.prune_dpd_workspace_bytes.restype = ctypes.c_size_t
+    lib.prune_model_last_error.argtypes = [P]
+    lib.prune_model_last_error.restype = ctypes.c_char_p
     lib.prune_server_last_error.argtypes = [P]
     lib.prune_server_last_error.restype = ctypes.c_char_p
     return lib
@@ -148,9 +169,11 @@ def lib():
     return _LIB
 
 
-def check(status: int, g=None, batch=None, server=None):
+def check(status: int, g=None, batch=None, server=None, model=None):
     if status != PRUNE_OK:
-        if server is not None:
+        if model is not None:
+            msg = lib().prune_model_last_error(model).decode(errors="replace")
+        elif server is not None:
             msg = lib().prune_server_last_error(server).decode(errors="replace")
         elif batch is not None:
             msg = lib().prune_batch_last_error(batch).decode(errors="replace")
