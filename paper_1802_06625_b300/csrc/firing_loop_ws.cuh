@@ -1,0 +1,540 @@
+// Warp-specialised fused firing loop on tcgen05 (N = 32, T <= 65): the same
+// arithmetic as firing_loop_tc_kernel (block-Toeplitz FIR and HX_b on
+// tensor cores, split FP16, look-back control), with the phases of a tile
+// split over roles that run concurrently on different tiles:
+//
+//   warp 0          producer: claims tiles (ticket order, frame window),
+//                   checks FIR's firing rule on f0 and copies the raw input
+//                   tile (+ halo) into a 2-stage shared-memory ring with bulk
+//                   asynchronous copies (cp.async.bulk, mbarrier tx counts);
+//   warp 1          MMA: the FIR GEMMs of a tile into one of 4 TMEM slots;
+//   warps 2-5       converter: raw FP32 -> split-FP16 chunk array (the
+//                   permuted K-major 128B-swizzle operand), 2-buffer ring;
+//   warps 6-17      three epilogue groups, tiles taken round-robin: block
+//                   energies, DET and SEL, the HX_b operand written back into
+//                   the slot's free TMEM columns (two FP16 per column), HX_b as
+//                   a GEMM with its A operand in tensor memory on all 128 rows,
+//                   the look-back (overlapping the HX GEMM), the SINK payload
+//                   of the selected rows and the frame completion.
+//
+// A TMEM slot is 128 columns: the FIR accumulator (FP32, columns 0-63)
+// whose rows are split into the HX operand (hi in 64-95, lo in 96-127), and
+// the HX accumulator written over columns 0-63.  Every hand-off is an
+// mbarrier whose phase flips exactly once per use, so each waiter knows the
+// parity from the use count.  After the last tile the producer sends one
+// sentinel item per epilogue group through the pipeline.  Every wait is
+// bounded and also returns when the CTA's stop flag is set; each MMA issuer
+// waits for its own last commit before tensor memory is freed.
+#pragma once
+#include "firing_loop_tc.cuh"
+
+namespace prune {
+
+constexpr int kWsWarps = 18;
+constexpr int kWsThreads = kWsWarps * 32;     // 576
+constexpr int kWsGroups = 3;                  // epilogue groups
+constexpr int kWsSlots = 4;                   // TMEM slots of 128 columns
+constexpr int kWsRawHalo = 64;                // halo samples staged (S <= 2)
+constexpr uint32_t kWsRawBytes = ((kWsRawHalo + kTTile) * 8 + 1023) / 1024 * 1024;  // 33 KB
+constexpr uint32_t kWsAOpBytes = 2u * (kTGroups + 2) * 1024;                       // 36 KB (hi | lo)
+constexpr uint32_t kWsMiscBytes = 8192;
+
+__host__ __device__ inline bool ws_loop_supported(int T) { return tc_shifts(T) <= 3; }
+// constants (FIR ns x hi/lo, HX hi/lo) | 2 raw stages | 2 operand buffers | misc
+__host__ __device__ inline size_t ws_loop_smem_bytes(int T) {
+  return 1024 + static_cast<size_t>(tc_shifts(T)) * 2 * kTOpBytes + 2 * kTOpBytes + 2 * kWsRawBytes +
+         2 * kWsAOpBytes + kWsMiscBytes;
+}
+
+// Per-item record passed along the pipeline (t = ~0: sentinel).
+struct WsItem {
+  unsigned long long t;
+  int32_t k, tile, nv, pad;
+};
+
+// Shared scratch of one epilogue group.
+struct WsGroup {
+  float eth[128];
+  float Et[128];
+  int32_t rank[128];
+  float red4[4];
+  int32_t cnt;
+  int32_t pad;
+  long long prefix;
+};
+
+// Bounded mbarrier wait that also gives up when the CTA's stop flag is set.
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, uint64_t timeout_ns,
+                                        const volatile int32_t *stop) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    if ((it & 127u) == 0u && (*stop || globaltimer_ns() - t0 > timeout_ns)) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+// A in tensor memory, B in shared memory.
+__device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&w)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
+               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+  return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(a))) |
+         (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(b))) << 16);
+}
+
+static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(TcLoopParams tp) {
+  extern __shared__ unsigned char smem_raw[];
+  const LoopParams &p = tp.lp;
+  const FirParams &f = p.f;
+  const int ns = tp.ns, S = ns - 1;
+  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *bfir = base;
+  unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
+  unsigned char *raw0 = bhx + 2 * kTOpBytes;
+  unsigned char *aop0 = raw0 + 2 * kWsRawBytes;
+  unsigned char *misc = aop0 + 2 * kWsAOpBytes;
+  uint64_t *raw_full = reinterpret_cast<uint64_t *>(misc);          // [2]
+  uint64_t *raw_empty = raw_full + 2;                               // [2]
+  uint64_t *a_full = raw_empty + 2;                                 // [2]
+  uint64_t *a_empty = a_full + 2;                                   // [2]
+  uint64_t *fir_full = a_empty + 2;                                 // [4]
+  uint64_t *slot_empty = fir_full + 4;                              // [4]
+  uint64_t *hx_full = slot_empty + 4;                               // [4]
+  WsItem *item_raw = reinterpret_cast<WsItem *>(misc + 256);        // [2]
+  WsItem *item_a = item_raw + 2;                                    // [2]
+  WsItem *item_slot = item_a + 2;                                   // [4]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 512);
+  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 520);
+  WsGroup *grp = reinterpret_cast<WsGroup *>(misc + 1024);          // [3]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
+  const unsigned long long kSentinel = ~0ull;
+
+  // ---- setup: constant operands, barriers, tensor memory
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(tp.fir_ops);
+    uint4 *dst = reinterpret_cast<uint4 *>(bfir);
+    for (int q = tid; q < static_cast<int>(ns * 2 * kTOpBytes / 16); q += kWsThreads) dst[q] = src[q];
+    const uint4 *hsrc = reinterpret_cast<const uint4 *>(tp.hx_ops);
+    uint4 *hdst = reinterpret_cast<uint4 *>(bhx);
+    for (int q = tid; q < static_cast<int>(2 * kTOpBytes / 16); q += kWsThreads) hdst[q] = hsrc[q];
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 20; ++i) mbar_init(smem_u32(raw_full + i), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *stop = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&](uint32_t actor, uint32_t where, uint64_t frame) {
+    if (!*stop) {
+      report_error(p.status, kDevTimeout, actor, where, frame);
+      atomicExch(&p.ls->abort, 1u);
+    }
+    *stop = 1;
+  };
+
+  if (warp == 0) {
+    // ================================================================ producer
+    uint64_t f0_seen = 0;
+    int sentinels = 0;
+    bool claimed_out = false;  // one failing claim per CTA
+    for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !ws_wait(smem_u32(&raw_empty[s]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop)) {
+        if (lane == 0) fail(kActFir, 10, 0);
+        break;
+      }
+      unsigned long long t = kSentinel;
+      if (lane == 0 && !claimed_out) {
+        t = atomicAdd(&p.ls->ticket, 1ull) - p.ticket_base;
+        if (ld_volatile_u32(&p.ls->abort) || *stop) t = kSentinel;
+      }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= total) {  // no more tiles: one sentinel per epilogue group
+        claimed_out = true;
+        if (lane == 0) {
+          item_raw[s] = WsItem{kSentinel, 0, 0, 0, 0};
+          mbar_arrive(smem_u32(&raw_full[s]));
+        }
+        ++sentinels;
+        continue;
+      }
+      int k, tile;
+      tc_ticket_tile(t, f.frames, f.tiles, tp.window, &k, &tile);
+      const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
+      const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
+      const int nv = static_cast<int>(min(static_cast<int64_t>(kTTile), f.L - s0));
+      // FIR's firing rule on f0 (bounded)
+      int ok = 1;
+      if (lane == 0) {
+        const uint64_t need = (seq + 1) * static_cast<uint64_t>(f.F);
+        if (f0_seen < need)
+          ok = bounded_wait(p, [&] {
+            f0_seen = ld_acquire_u64(&p.ctr[0 * 3 + kCtrWritten]);
+            return f0_seen >= need;
+          }, kActFir, 0, seq);
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) *stop = 1;
+        break;
+      }
+      const float2 *cur = f.src.frame(k);
+      unsigned char *raw = raw0 + s * kWsRawBytes;  // sample s0 - 64 at byte 0
+      const uint32_t halo = static_cast<uint32_t>(S) * kTR;        // staged halo samples (<= 64)
+      const uint32_t hoff = (kWsRawHalo - halo) * 8;               // halo starts here
+      if (tile == 0 && k == 0) {  // delay token (or zeros) as the halo: plain stores
+        for (int m = lane; m < static_cast<int>(halo); m += 32) {
+          const int d = static_cast<int>(halo) - m;                // samples before s0
+          float2 v = make_float2(0.f, 0.f);
+          if (d <= f.T - 1 && f.hist) v = f.hist[f.T - 1 - d];
+          reinterpret_cast<float2 *>(raw + hoff)[m] = v;
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        item_raw[s] = WsItem{t, k, tile, nv, 0};
+        uint32_t bytes = static_cast<uint32_t>(nv) * 8;
+        if (tile > 0) bytes += halo * 8;
+        else if (k > 0) bytes += halo * 8;
+        mbar_arrive_tx(smem_u32(&raw_full[s]), bytes);
+        if (tile > 0) {
+          bulk_g2s(smem_u32(raw + hoff), cur + s0 - halo, (halo + static_cast<uint32_t>(nv)) * 8,
+                   smem_u32(&raw_full[s]));
+        } else {
+          bulk_g2s(smem_u32(raw + kWsRawHalo * 8), cur, static_cast<uint32_t>(nv) * 8, smem_u32(&raw_full[s]));
+          if (k > 0 && halo > 0)
+            bulk_g2s(smem_u32(raw + hoff), f.src.frame(k - 1) + f.L - halo, halo * 8, smem_u32(&raw_full[s]));
+        }
+      }
+      // the delay token after the run: the last T-1 input samples
+      if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
+        for (int m = lane; m < f.T - 1; m += 32) f.hist_out[m] = cur[f.L - (f.T - 1) + m];
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA
+    int sentinels = 0;
+    uint32_t last_bar = 0, last_par = 0;
+    bool issued = false;
+    for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
+      const int b = i & 1, j = i & 3;
+      if (!ws_wait(smem_u32(&a_full[b]), (i >> 1) & 1u, p.timeout_ns, stop)) {
+        if (lane == 0) fail(kActFir, 11, 0);
+        break;
+      }
+      if (i >= kWsSlots && !ws_wait(smem_u32(&slot_empty[j]), ((i >> 2) - 1) & 1u, p.timeout_ns, stop)) {
+        if (lane == 0) fail(kActFir, 12, 0);
+        break;
+      }
+      const WsItem it = item_a[b];
+      if (lane == 0) {
+        item_slot[j] = it;
+        if (it.t == kSentinel) {
+          mbar_arrive(smem_u32(&fir_full[j]));
+          mbar_arrive(smem_u32(&a_empty[b]));
+        } else {
+          tc_fence_after();
+          const unsigned char *a = aop0 + b * kWsAOpBytes;
+          const uint32_t ah = smem_u32(a), al = ah + (kTGroups + S) * 1024u, b0 = smem_u32(bfir);
+          const uint32_t d = tmem + static_cast<uint32_t>(j * 128);
+          for (int sh = 0; sh < ns; ++sh) {
+            const uint32_t arow = static_cast<uint32_t>(S - sh) * 1024u;  // group -sh
+            const uint32_t pa[3] = {ah + arow, ah + arow, al + arow};
+            const uint32_t bh = b0 + static_cast<uint32_t>(2 * sh) * kTOpBytes, bl = bh + kTOpBytes;
+            const uint32_t pb[3] = {bh, bl, bh};
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                umma_f16(d, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32), kTIdescN64,
+                         (sh > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+          }
+          umma_commit(smem_u32(&fir_full[j]));
+          umma_commit(smem_u32(&a_empty[b]));
+          issued = true;
+          last_bar = smem_u32(&a_empty[b]);
+          last_par = (i >> 1) & 1u;
+        }
+      }
+      __syncwarp();
+      if (it.t == kSentinel) ++sentinels;
+    }
+    if (lane == 0 && issued && *stop) mbar_wait_bounded(last_bar, last_par, p.timeout_ns);
+  } else if (warp < 6) {
+    // ================================================================ converter
+    const int ct = tid - 64;  // 0..127
+    int sentinels = 0;
+    for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
+      const int s = i & 1, b = i & 1;
+      if (!ws_wait(smem_u32(&raw_full[s]), (i >> 1) & 1u, p.timeout_ns, stop)) {
+        if (ct == 0) fail(kActFir, 13, 0);
+        break;
+      }
+      if (i >= 2 && !ws_wait(smem_u32(&a_empty[b]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop)) {
+        if (ct == 0) fail(kActFir, 14, 0);
+        break;
+      }
+      const WsItem it = item_raw[s];
+      if (it.t != kSentinel) {
+        const unsigned char *raw = raw0 + s * kWsRawBytes;
+        unsigned char *ahi = aop0 + b * kWsAOpBytes;
+        unsigned char *alo = ahi + (kTGroups + S) * 1024;
+        const int npieces = (kTGroups + S) * 64;
+        for (int q = ct; q < npieces; q += 128) {
+          const int row = q >> 3, pc = q & 7;
+          const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
+          float v[8];
+          if (kTR * j + 4 * pc < it.nv) {
+            const float4 *src =
+                reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
+            const float4 u0 = src[0], u1 = src[1];
+            v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+            v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+          }
+          const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v, false);
+          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v, true);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (ct == 0) {
+        item_a[b] = it;
+        mbar_arrive(smem_u32(&a_full[b]));
+        mbar_arrive(smem_u32(&raw_empty[s]));
+      }
+      if (it.t == kSentinel) ++sentinels;
+    }
+  } else {
+    // ================================================================ epilogue
+    const int e = (warp - 6) >> 2;              // group 0..2
+    const int gt = tid - 192 - 128 * e;         // 0..127
+    const int gw = gt >> 5;                     // warp within the group
+    const int q4 = warp & 3;                    // TMEM lane quarter of this warp
+    const int m = q4 * 32 + lane;               // GEMM row (TMEM lane) owned by this thread
+    const int jc = 16 * (m & 7) + (m >> 3);     // output chunk of row m
+    const uint32_t tlane = static_cast<uint32_t>(q4 * 32) << 16;
+    WsGroup &G = grp[e];
+    const int bar = 2 + e;
+    auto gsync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory"); };
+    const int rpb = f.B / kTR;
+    bool hx_issued = false;
+    uint32_t hx_last_par = 0, hx_last_bar = 0;
+    for (uint32_t i = static_cast<uint32_t>(e);; i += kWsGroups) {
+      const int j = i & 3;
+      const uint32_t use = i >> 2;
+      if (!ws_wait(smem_u32(&fir_full[j]), use & 1u, p.timeout_ns, stop)) {
+        if (gt == 0) fail(kActFir, 15, 0);
+        break;
+      }
+      const WsItem it = item_slot[j];
+      if (it.t == kSentinel) break;
+      tc_fence_after();
+      const int k = it.k, tile = it.tile, nv = it.nv;
+      const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
+      const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
+      const int rows_valid = nv / kTR;
+      const uint32_t slot = tmem + static_cast<uint32_t>(j * 128);
+      // ---- energies of the FIR rows; the rows split into the HX operand
+      //      (hi in columns 64-95, lo in 96-127, two FP16 per column)
+      {
+        float en = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          float v[16];
+          tmem_ld16(slot + tlane + static_cast<uint32_t>(16 * c4), v);
+          tmem_ld_wait();
+          uint32_t hi[8], lo[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            en = fmaf(v[2 * q], v[2 * q], en);
+            en = fmaf(v[2 * q + 1], v[2 * q + 1], en);
+            const float y0 = v[2 * q] * (1.f / kTScale), y1 = v[2 * q + 1] * (1.f / kTScale);
+            const __half h0 = __float2half_rn(y0), h1 = __float2half_rn(y1);
+            hi[q] = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+            lo[q] = pack_half2(y0 - __half2float(h0), y1 - __half2float(h1));
+          }
+          tmem_st8(slot + tlane + 64u + static_cast<uint32_t>(8 * c4), hi);
+          tmem_st8(slot + tlane + 96u + static_cast<uint32_t>(8 * c4), lo);
+        }
+        G.eth[jc] = jc < rows_valid ? en * (1.f / (kTScale * kTScale)) : 0.f;
+        tmem_st_wait();
+      }
+      tc_fence_before();
+      gsync();
+      // ---- block energies (fixed order), DET, SEL inside the tile
+      const int nb = nv / f.B;
+      {
+        float v = G.eth[gt];
+        const int seg = rpb < 32 ? rpb : 32;
+        for (int off = seg >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (rpb <= 32) {
+          if ((gt & (seg - 1)) == 0 && gt / rpb < nb) G.Et[gt / rpb] = v;
+        } else {
+          if (lane == 0) G.red4[gw] = v;
+        }
+        gsync();
+        if (rpb > 32 && gt < nb) {
+          float E = 0.f;
+          for (int w = 0; w < rpb / 32; ++w) E += G.red4[gt * (rpb / 32) + w];
+          G.Et[gt] = E;
+        }
+        gsync();
+        if (f.energy && gt < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + gt] = G.Et[gt];
+      }
+      if (gw == 0) {
+        int cnt = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+          const int b = b0 + lane;
+          const bool v = b < nb && G.Et[b] > p.tau;
+          const unsigned msk = __ballot_sync(0xffffffffu, v);
+          if (b < nb) G.rank[b] = v ? cnt + __popc(msk & ((1u << lane) - 1u)) : -1;
+          cnt += __popc(msk);
+        }
+        if (lane == 0) G.cnt = cnt;
+      }
+      gsync();
+      const int cnt = G.cnt;
+      // ---- HX_b GEMM on all 128 rows, A in tensor memory (the phase of
+      //      hx_full flips once per use: a plain arrive when nothing is selected)
+      if (gt == 0) {
+        if (cnt > 0) {
+          tc_fence_after();
+          const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
+          const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
+          const uint32_t pb[3] = {bh, bl, bh};
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
+                          kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
+          umma_commit(smem_u32(&hx_full[j]));
+          hx_issued = true;
+          hx_last_bar = smem_u32(&hx_full[j]);
+          hx_last_par = use & 1u;
+        } else {
+          mbar_arrive(smem_u32(&hx_full[j]));
+        }
+      }
+      // ---- look-back for the tile's offset in the frame (overlaps the GEMM)
+      const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
+      if (gw == 0) {
+        const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
+        if (lane == 0) G.prefix = pr;
+      }
+      gsync();
+      const long long prefix = G.prefix;
+      if (prefix < 0 || prefix + cnt > f.F) {
+        if (gt == 0 && prefix >= 0) {
+          report_error(p.status, kDevInvariant, kActSel, 6, seq);
+          atomicExch(&p.ls->abort, 1u);
+        }
+        if (gt == 0) *stop = 1;
+        break;
+      }
+      const int64_t rs = p.rslot.slot(k);
+      if (gt < nb && G.rank[gt] >= 0) p.rec_idx[rs * f.F + prefix + G.rank[gt]] = static_cast<int32_t>(s0 / f.B) + gt;
+      // ---- SINK payload: the selected rows at their compacted places
+      if (!ws_wait(smem_u32(&hx_full[j]), use & 1u, p.timeout_ns, stop)) {
+        if (gt == 0) fail(kActHx, 7, seq);
+        break;
+      }
+      tc_fence_after();
+      if (cnt > 0) {
+        const int rk = jc < rows_valid ? G.rank[jc / rpb] : -1;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          float o[32];
+          {
+            float t16[16];
+            tmem_ld16(slot + tlane + static_cast<uint32_t>(hf * 32), t16);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[q] = t16[q];
+            tmem_ld16(slot + tlane + static_cast<uint32_t>(hf * 32 + 16), t16);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) o[16 + q] = t16[q];
+            tmem_ld_wait();
+          }
+          if (rk >= 0) {
+            float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
+                                                     hf * 16);
+            const float sc = 1.f / kTScale;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              dst[q] = make_float4(o[4 * q] * sc, o[4 * q + 1] * sc, o[4 * q + 2] * sc, o[4 * q + 3] * sc);
+          }
+        }
+      }
+      // ---- frame completion; the slot goes back to the MMA warp
+      tc_fence_before();
+      gsync();
+      if (gw == 0) {
+        int last = 0;
+        if (lane == 0) {
+          mbar_arrive(smem_u32(&slot_empty[j]));
+          __threadfence();
+          const uint32_t old = atomicAdd(&p.done[fslot], 1u);
+          if (old + 1u == static_cast<uint32_t>(f.tiles)) {
+            p.done[fslot] = 0u;
+            const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
+            p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
+            p.rec_frame[rs] = static_cast<int64_t>(seq);
+            __threadfence();
+            st_release_u64(&p.ready[fslot], seq + 1);
+            __threadfence();
+            last = 1;
+          }
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames, lane);
+      }
+    }
+    if (gt == 0 && hx_issued && *stop) mbar_wait_bounded(hx_last_bar, hx_last_par, p.timeout_ns);
+  }
+
+  // ---- leave: every role is done (or stopped); free tensor memory
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
+}  // namespace prune

@@ -22,6 +22,7 @@
 #include "firing_loop.cuh"
 #include "hx_tc.cuh"
 #include "firing_loop_tc.cuh"
+#include "firing_loop_ws.cuh"
 
 using namespace prune;
 
@@ -100,6 +101,7 @@ struct prune_graph {
   uint64_t *ready = nullptr;          // [C] record-final flags (frame seq + 1)
   unsigned long long ticket_base = 0;
   uint64_t timeout_ns = 2000000000ull;
+  bool ws_loop = true;  // warp-specialised tensor-core loop (PRUNE_TC_KERNEL=pipes: tile pipelines)
   uint16_t *hx_b_ops = nullptr;       // tcgen05 B operands (N >= 64)
   uint16_t *tc_fir_ops = nullptr;     // tensor-core firing loop: FIR tap operands
   uint16_t *tc_hx_ops = nullptr;      //   and the real form of H
@@ -298,6 +300,14 @@ static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
   return PRUNE_OK;
 }
 
+static cudaError_t launch_ws_loop(const TcLoopParams &tp, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(firing_loop_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  firing_loop_ws_kernel<<<grid, kWsThreads, smem, s>>>(tp);
+  return cudaGetLastError();
+}
+
 template <int NP>
 static cudaError_t launch_tc_loop(const TcLoopParams &tp, int grid, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(firing_loop_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -359,6 +369,25 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
     tp.fir_ops = g->tc_fir_ops;
     tp.hx_ops = g->tc_hx_ops;
     tp.ns = tc_shifts(d.T);
+    // warp-specialised loop for T <= 65 unless PRUNE_TC_KERNEL=pipes asks
+    // for the tile-pipeline loop
+    if (g->ws_loop && ws_loop_supported(d.T)) {
+      const size_t wsmem = ws_loop_smem_bytes(d.T);
+      const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
+      const int grid = static_cast<int>(std::max<unsigned long long>(
+          1, std::min<unsigned long long>(ttotal, static_cast<unsigned long long>(g->sms))));
+      // about 8 tiles of one frame in flight; a CTA holds up to 8 tiles
+      tp.window = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(n, grid)));
+      cudaError_t e;
+      {
+        KTimer kt(g, 6);
+        e = launch_ws_loop(tp, grid, wsmem, g->stream);
+      }
+      if (e != cudaSuccess)
+        return fail(g, PRUNE_ECUDA, std::string("tensor-core firing loop launch: ") + cudaGetErrorString(e));
+      g->ticket_base += ttotal + static_cast<unsigned long long>(grid);  // one failing claim per CTA
+      return PRUNE_OK;
+    }
     const size_t smem = tc_loop_smem_bytes(d.T);
     const int np = tc_pipes(d.T);
     const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
@@ -504,6 +533,7 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
       (s = galloc(g, &g->loop, 1)) || (s = galloc(g, &g->look, static_cast<size_t>(C) * g->tiles)) ||
       (s = galloc(g, &g->done, static_cast<size_t>(C))) || (s = galloc(g, &g->ready, static_cast<size_t>(C))))
     return bail(s);
+  if (const char *kk = std::getenv("PRUNE_TC_KERNEL")) g->ws_loop = std::string(kk) != "pipes";
   if (const char *tm = std::getenv("PRUNE_TIMEOUT_MS")) {
     const long long ms = std::atoll(tm);
     if (ms > 0) g->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
