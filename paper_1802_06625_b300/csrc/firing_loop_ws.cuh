@@ -94,15 +94,40 @@ __device__ __forceinline__ void umma_f16_ts(uint32_t tmem_d, uint32_t tmem_a, ui
       "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&w)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
-               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
-               : "memory");
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&w)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+      "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+      : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns per warp.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
-  return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(a))) |
-         (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(b))) << 16);
+// Split a pair of FP32 values into FP16 hi and lo parts, packed two per
+// 32-bit word (first value in the low half): hi keeps the top 10 explicit
+// mantissa bits (x with its low 13 bits cleared, exact in FP16 within FP16's
+// normal range), lo = x - hi (exact in FP32) rounded to FP16, so
+// hi + lo = x within 2^-21 |x|.  Two paired conversions per pair.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo) {
+  const float ah = __uint_as_float(__float_as_uint(a) & 0xFFFFE000u);
+  const float bh = __uint_as_float(__float_as_uint(b) & 0xFFFFE000u);
+  const __half2 h = __floats2half2_rn(ah, bh), l = __floats2half2_rn(a - ah, b - bh);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(TcLoopParams tp) {
@@ -328,8 +353,13 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
             for (int e = 0; e < 8; ++e) v[e] = 0.f;
           }
           const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v, false);
-          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v, true);
+          uint4 h4, l4;
+          split_pair(v[0], v[1], h4.x, l4.x);
+          split_pair(v[2], v[3], h4.y, l4.y);
+          split_pair(v[4], v[5], h4.z, l4.z);
+          split_pair(v[6], v[7], h4.w, l4.w);
+          *reinterpret_cast<uint4 *>(ahi + off) = h4;
+          *reinterpret_cast<uint4 *>(alo + off) = l4;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -376,28 +406,44 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       {
         float en = 0.f;
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          float v[16];
-          tmem_ld16(slot + tlane + static_cast<uint32_t>(16 * c4), v);
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(slot + tlane + static_cast<uint32_t>(32 * h), v);
           tmem_ld_wait();
-          uint32_t hi[8], lo[8];
+          uint32_t hi[16], lo[16];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 16; ++q) {
             en = fmaf(v[2 * q], v[2 * q], en);
             en = fmaf(v[2 * q + 1], v[2 * q + 1], en);
-            const float y0 = v[2 * q] * (1.f / kTScale), y1 = v[2 * q + 1] * (1.f / kTScale);
-            const __half h0 = __float2half_rn(y0), h1 = __float2half_rn(y1);
-            hi[q] = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
-            lo[q] = pack_half2(y0 - __half2float(h0), y1 - __half2float(h1));
+            split_pair(v[2 * q] * (1.f / kTScale), v[2 * q + 1] * (1.f / kTScale), hi[q], lo[q]);
           }
-          tmem_st8(slot + tlane + 64u + static_cast<uint32_t>(8 * c4), hi);
-          tmem_st8(slot + tlane + 96u + static_cast<uint32_t>(8 * c4), lo);
+          tmem_st16(slot + tlane + 64u + static_cast<uint32_t>(16 * h), hi);
+          tmem_st16(slot + tlane + 96u + static_cast<uint32_t>(16 * h), lo);
         }
         G.eth[jc] = jc < rows_valid ? en * (1.f / (kTScale * kTScale)) : 0.f;
         tmem_st_wait();
       }
       tc_fence_before();
       gsync();
+      // ---- HX_b GEMM on all 128 rows with its A operand in tensor memory,
+      //      issued before DET and SEL so that it overlaps them and the
+      //      look-back (rows of unselected blocks are computed and dropped)
+      if (gt == 0) {
+        tc_fence_after();
+        const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
+        const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
+        const uint32_t pb[3] = {bh, bl, bh};
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
+                        kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
+        umma_commit(smem_u32(&hx_full[j]));
+        hx_issued = true;
+        hx_last_bar = smem_u32(&hx_full[j]);
+        hx_last_par = use & 1u;
+      }
       // ---- block energies (fixed order), DET, SEL inside the tile
       const int nb = nv / f.B;
       {
@@ -410,56 +456,35 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           if (lane == 0) G.red4[gw] = v;
         }
         gsync();
-        if (rpb > 32 && gt < nb) {
-          float E = 0.f;
-          for (int w = 0; w < rpb / 32; ++w) E += G.red4[gt * (rpb / 32) + w];
-          G.Et[gt] = E;
+        if (rpb > 32) {
+          if (gt < nb) {
+            float E = 0.f;
+            for (int w = 0; w < rpb / 32; ++w) E += G.red4[gt * (rpb / 32) + w];
+            G.Et[gt] = E;
+          }
+          gsync();
         }
-        gsync();
         if (f.energy && gt < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + gt] = G.Et[gt];
       }
+      int cnt_w0 = 0;  // warp 0: selected blocks, known before the look-back
       if (gw == 0) {
-        int cnt = 0;
         for (int b0 = 0; b0 < nb; b0 += 32) {
           const int b = b0 + lane;
           const bool v = b < nb && G.Et[b] > p.tau;
           const unsigned msk = __ballot_sync(0xffffffffu, v);
-          if (b < nb) G.rank[b] = v ? cnt + __popc(msk & ((1u << lane) - 1u)) : -1;
-          cnt += __popc(msk);
+          if (b < nb) G.rank[b] = v ? cnt_w0 + __popc(msk & ((1u << lane) - 1u)) : -1;
+          cnt_w0 += __popc(msk);
         }
-        if (lane == 0) G.cnt = cnt;
-      }
-      gsync();
-      const int cnt = G.cnt;
-      // ---- HX_b GEMM on all 128 rows, A in tensor memory (the phase of
-      //      hx_full flips once per use: a plain arrive when nothing is selected)
-      if (gt == 0) {
-        if (cnt > 0) {
-          tc_fence_after();
-          const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
-          const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
-          const uint32_t pb[3] = {bh, bl, bh};
-#pragma unroll
-          for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
-                          kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
-          umma_commit(smem_u32(&hx_full[j]));
-          hx_issued = true;
-          hx_last_bar = smem_u32(&hx_full[j]);
-          hx_last_par = use & 1u;
-        } else {
-          mbar_arrive(smem_u32(&hx_full[j]));
-        }
+        if (lane == 0) G.cnt = cnt_w0;
       }
       // ---- look-back for the tile's offset in the frame (overlaps the GEMM)
       const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
       if (gw == 0) {
-        const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
+        const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt_w0, seq, lane);
         if (lane == 0) G.prefix = pr;
       }
       gsync();
+      const int cnt = G.cnt;
       const long long prefix = G.prefix;
       if (prefix < 0 || prefix + cnt > f.F) {
         if (gt == 0 && prefix >= 0) {
@@ -482,16 +507,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
           float o[32];
-          {
-            float t16[16];
-            tmem_ld16(slot + tlane + static_cast<uint32_t>(hf * 32), t16);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) o[q] = t16[q];
-            tmem_ld16(slot + tlane + static_cast<uint32_t>(hf * 32 + 16), t16);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) o[16 + q] = t16[q];
-            tmem_ld_wait();
-          }
+          tmem_ld32(slot + tlane + static_cast<uint32_t>(hf * 32), o);
+          tmem_ld_wait();
           if (rk >= 0) {
             float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
                                                      hf * 16);
