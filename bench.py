@@ -560,7 +560,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
     ap.add_argument("--frames", type=int, default=0, help="frames per step (default: the workload's)")
-    ap.add_argument("--C", type=int, default=48,
+    ap.add_argument("--C", type=int, default=336,
                     help="buffering constant of eq. (2): frames f0 holds, hence frames one launch can fire")
     ap.add_argument("--path", default="fused", choices=["fused", "cuda_cores", "actors"],
                     help="fused loop (tensor cores where the shape allows), fused loop on CUDA cores, "

@@ -376,8 +376,12 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
       const unsigned long long ttotal = static_cast<unsigned long long>(n) * tp.lp.f.tiles;
       const int grid = static_cast<int>(std::max<unsigned long long>(
           1, std::min<unsigned long long>(ttotal, static_cast<unsigned long long>(g->sms))));
-      // about 8 tiles of one frame in flight; a CTA holds up to 8 tiles
-      tp.window = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(n, grid)));
+      // Frames fired round-robin: a CTA holds up to about 8 tiles in flight,
+      // so a window of 8 x grid frames leaves about one tile of a frame in
+      // flight (short look-backs); PRUNE_TC_WINDOW overrides the factor.
+      int64_t wf = 8;
+      if (const char *wv = std::getenv("PRUNE_TC_WINDOW")) wf = std::max<int64_t>(1, std::atoll(wv));
+      tp.window = static_cast<int32_t>(std::max<int64_t>(1, std::min<int64_t>(n, wf * grid)));
       cudaError_t e;
       {
         KTimer kt(g, 6);
