@@ -80,16 +80,18 @@ __device__ __forceinline__ bool bounded_wait(const LoopParams &p, Pred pred, uin
 
 // Decoupled look-back, one warp: publish the tile's count as an aggregate,
 // then read 32 predecessors per round trip, summing aggregates back to the
-// nearest inclusive prefix; publish the inclusive prefix.  Waits (only when
+// nearest inclusive prefix; publish the inclusive prefix.  A look-back word
+// (epoch, flag, count) carries everything its readers use, so relaxed
+// GPU-scope accesses suffice: nothing else is read on the strength of it.  Waits (only when
 // a predecessor has not published anything yet) are bounded.  Returns the
 // exclusive prefix on every lane, or -1 on timeout / abort.
 __device__ __forceinline__ int64_t lookback_warp(const LoopParams &p, uint64_t *words, int tile, uint64_t epoch,
                                                  uint32_t cnt, uint64_t frame, int lane) {
   if (tile == 0) {
-    if (lane == 0) st_release_u64(&words[0], look_pack(epoch, kLookPrefix, cnt));
+    if (lane == 0) st_relaxed_u64(&words[0], look_pack(epoch, kLookPrefix, cnt));
     return 0;
   }
-  if (lane == 0) st_release_u64(&words[tile], look_pack(epoch, kLookAgg, cnt));
+  if (lane == 0) st_relaxed_u64(&words[tile], look_pack(epoch, kLookAgg, cnt));
   uint64_t prefix = 0;
   int i0 = tile - 1;
   uint64_t t0 = 0;
@@ -98,7 +100,7 @@ __device__ __forceinline__ int64_t lookback_warp(const LoopParams &p, uint64_t *
     const int i = i0 - lane;
     uint32_t flag = kLookPrefix, val = 0;  // i < 0: tile 0 always publishes a prefix first
     if (i >= 0) {
-      const uint64_t w = ld_acquire_u64(&words[i]);
+      const uint64_t w = ld_relaxed_u64(&words[i]);
       flag = (w >> 34) == epoch ? static_cast<uint32_t>((w >> 32) & 3u) : 0u;
       val = static_cast<uint32_t>(w);
     }
@@ -131,7 +133,7 @@ __device__ __forceinline__ int64_t lookback_warp(const LoopParams &p, uint64_t *
     if (incl) break;
     i0 -= 32;
   }
-  if (lane == 0) st_release_u64(&words[tile], look_pack(epoch, kLookPrefix, static_cast<uint32_t>(prefix + cnt)));
+  if (lane == 0) st_relaxed_u64(&words[tile], look_pack(epoch, kLookPrefix, static_cast<uint32_t>(prefix + cnt)));
   return static_cast<int64_t>(prefix);
 }
 
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(kFirThreads) firing_loop_kernel(LoopParams p) 
         const uint32_t old = atomicAdd(&p.done[fslot], 1u);
         if (old + 1u == static_cast<uint32_t>(f.tiles)) {
           p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
+          __threadfence();  // every tile counted: their look-back words are visible
           const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
           const uint32_t c = static_cast<uint32_t>(w);
           p.rec_c[rs] = static_cast<int32_t>(c);

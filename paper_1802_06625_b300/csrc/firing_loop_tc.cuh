@@ -524,6 +524,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
         const uint32_t old = atomicAdd(&p.done[fslot], 1u);
         if (old + 1u == static_cast<uint32_t>(f.tiles)) {
           p.done[fslot] = 0u;  // every tile of the frame has counted: reset the slot
+          __threadfence();  // every tile counted: their look-back words are visible
           const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
           p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
           p.rec_frame[rs] = static_cast<int64_t>(seq);
