@@ -40,7 +40,7 @@ METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 lat
 # kind, from one ncu capture of the kernel as it stands (8-frame launch,
 # dram__bytes_read.sum + dram__bytes_write.sum divided by 8); scaled to a
 # launch by the frames it fires.  Remove an entry when its kernel changes.
-TRAFFIC_PER_FRAME = {}
+TRAFFIC_PER_FRAME = {6: (1612.04e6 + 807.51e6) / 48}
 UNIT = "Msamples/s"
 # FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
 # FP32 lanes x 2 flop x 2.032 GHz.
