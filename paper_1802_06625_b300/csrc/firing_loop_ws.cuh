@@ -13,9 +13,10 @@
 //   warps 6-17      three epilogue groups, tiles taken round-robin: block
 //                   energies, DET and SEL, the HX_b operand written back into
 //                   the slot's free TMEM columns (two FP16 per column), HX_b as
-//                   a GEMM with its A operand in tensor memory on all 128 rows,
-//                   the look-back (overlapping the HX GEMM), the SINK payload
-//                   of the selected rows and the frame completion.
+//                   a GEMM with its A operand in tensor memory on all 128 rows
+//                   (issued by the group's last warp), the look-back
+//                   (overlapping the HX GEMM), the SINK payload of the
+//                   selected rows and the frame completion.
 //
 // A TMEM slot is 128 columns: the FIR accumulator (FP32, columns 0-63)
 // whose rows are split into the HX operand (hi in 64-95, lo in 96-127), and
@@ -23,8 +24,9 @@
 // mbarrier whose phase flips exactly once per use, so each waiter knows the
 // parity from the use count.  After the last tile the producer sends one
 // sentinel item per epilogue group through the pipeline.  Every wait is
-// bounded and also returns when the CTA's stop flag is set; each MMA issuer
-// waits for its own last commit before tensor memory is freed.
+// bounded and also returns when the CTA's stop flag is set; before tensor
+// memory is freed, each thread that issued GEMMs commits once more to a
+// barrier of its own and waits for it (all its GEMMs have completed).
 #pragma once
 #include "firing_loop_tc.cuh"
 
@@ -149,6 +151,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   uint64_t *fir_full = a_empty + 2;                                 // [4]
   uint64_t *slot_empty = fir_full + 4;                              // [4]
   uint64_t *hx_full = slot_empty + 4;                               // [4]
+  uint64_t *fin = hx_full + 4;                                      // [4] one per issuer, at exit
   WsItem *item_raw = reinterpret_cast<WsItem *>(misc + 256);        // [2]
   WsItem *item_a = item_raw + 2;                                    // [2]
   WsItem *item_slot = item_a + 2;                                   // [4]
@@ -169,7 +172,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     for (int q = tid; q < static_cast<int>(2 * kTOpBytes / 16); q += kWsThreads) hdst[q] = hsrc[q];
   }
   if (tid == 0) {
-    for (int i = 0; i < 20; ++i) mbar_init(smem_u32(raw_full + i), 1);
+    for (int i = 0; i < 24; ++i) mbar_init(smem_u32(raw_full + i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *stop = 0;
   }
@@ -272,7 +275,6 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   } else if (warp == 1) {
     // ================================================================ MMA
     int sentinels = 0;
-    uint32_t last_bar = 0, last_par = 0;
     bool issued = false;
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
       const int b = i & 1, j = i & 3;
@@ -310,14 +312,15 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           umma_commit(smem_u32(&fir_full[j]));
           umma_commit(smem_u32(&a_empty[b]));
           issued = true;
-          last_bar = smem_u32(&a_empty[b]);
-          last_par = (i >> 1) & 1u;
         }
       }
       __syncwarp();
       if (it.t == kSentinel) ++sentinels;
     }
-    if (lane == 0 && issued && *stop) mbar_wait_bounded(last_bar, last_par, p.timeout_ns);
+    if (lane == 0 && issued) {  // every GEMM this thread issued has completed
+      umma_commit(smem_u32(&fin[0]));
+      mbar_wait_bounded(smem_u32(&fin[0]), 0u, p.timeout_ns);
+    }
   } else if (warp < 6) {
     // ================================================================ converter
     const int ct = tid - 64;  // 0..127
@@ -384,8 +387,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     const int bar = 2 + e;
     auto gsync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory"); };
     const int rpb = f.B / kTR;
+    constexpr int kHxIssuer = 96;               // lane 0 of the group's last warp
     bool hx_issued = false;
-    uint32_t hx_last_par = 0, hx_last_bar = 0;
     for (uint32_t i = static_cast<uint32_t>(e);; i += kWsGroups) {
       const int j = i & 3;
       const uint32_t use = i >> 2;
@@ -425,25 +428,6 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       }
       tc_fence_before();
       gsync();
-      // ---- HX_b GEMM on all 128 rows with its A operand in tensor memory,
-      //      issued before DET and SEL so that it overlaps them and the
-      //      look-back (rows of unselected blocks are computed and dropped)
-      if (gt == 0) {
-        tc_fence_after();
-        const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
-        const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
-        const uint32_t pb[3] = {bh, bl, bh};
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
-                        kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
-        umma_commit(smem_u32(&hx_full[j]));
-        hx_issued = true;
-        hx_last_bar = smem_u32(&hx_full[j]);
-        hx_last_par = use & 1u;
-      }
       // ---- block energies (fixed order), DET, SEL inside the tile
       const int nb = nv / f.B;
       {
@@ -465,6 +449,24 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           gsync();
         }
         if (f.energy && gt < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + gt] = G.Et[gt];
+      }
+      // ---- HX_b GEMM on all 128 rows with its A operand in tensor memory,
+      //      issued by the group's last warp while the first runs SEL and
+      //      the look-back (rows of unselected blocks are computed and
+      //      dropped); the issue waits for the tensor pipe's queue
+      if (gt == kHxIssuer) {
+        tc_fence_after();
+        const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
+        const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
+        const uint32_t pb[3] = {bh, bl, bh};
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
+                        kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
+        umma_commit(smem_u32(&hx_full[j]));
+        hx_issued = true;
       }
       int cnt_w0 = 0;  // warp 0: selected blocks, known before the look-back
       if (gw == 0) {
@@ -531,7 +533,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           if (old + 1u == static_cast<uint32_t>(f.tiles)) {
             p.done[fslot] = 0u;
             __threadfence();  // every tile counted: their look-back words are visible
-          const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
+            const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
             p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
             p.rec_frame[rs] = static_cast<int64_t>(seq);
             __threadfence();
@@ -543,7 +545,10 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         if (__shfl_sync(0xffffffffu, last, 0)) drain_bookkeeping(p, static_cast<uint64_t>(f.yslot.seq0) + f.frames, lane);
       }
     }
-    if (gt == 0 && hx_issued && *stop) mbar_wait_bounded(hx_last_bar, hx_last_par, p.timeout_ns);
+    if (gt == kHxIssuer && hx_issued) {
+      umma_commit(smem_u32(&fin[1 + e]));
+      mbar_wait_bounded(smem_u32(&fin[1 + e]), 0u, p.timeout_ns);
+    }
   }
 
   // ---- leave: every role is done (or stopped); free tensor memory
