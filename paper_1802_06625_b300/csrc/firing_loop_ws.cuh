@@ -59,7 +59,6 @@ struct WsGroup {
   float eth[128];
   float Et[128];
   int32_t rank[128];
-  float red4[4];
   int32_t cnt;
   int32_t pad;
   long long prefix;
@@ -117,6 +116,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
       : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&w)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
+               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Split a pair of FP32 values into FP16 hi and lo parts, packed two per
@@ -346,9 +350,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
           float v[8];
           if (kTR * j + 4 * pc < it.nv) {
+            // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read their
+            // halves in the other order, so each quarter-warp load covers all
+            // 32 banks once
             const float4 *src =
                 reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
-            const float4 u0 = src[0], u1 = src[1];
+            const int sw = (pc >> 2) & 1;
+            const float4 a0 = src[sw], a1 = src[sw ^ 1];
+            const float4 u0 = sw ? a1 : a0, u1 = sw ? a0 : a1;
             v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
             v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
           } else {
@@ -413,47 +422,29 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           float v[32];
           tmem_ld32(slot + tlane + static_cast<uint32_t>(32 * h), v);
           tmem_ld_wait();
-          uint32_t hi[16], lo[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            en = fmaf(v[2 * q], v[2 * q], en);
-            en = fmaf(v[2 * q + 1], v[2 * q + 1], en);
-            split_pair(v[2 * q] * (1.f / kTScale), v[2 * q + 1] * (1.f / kTScale), hi[q], lo[q]);
+          for (int qq = 0; qq < 2; ++qq) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int q0 = 0; q0 < 8; ++q0) {
+              const int q = 8 * qq + q0;
+              en = fmaf(v[2 * q], v[2 * q], en);
+              en = fmaf(v[2 * q + 1], v[2 * q + 1], en);
+              split_pair(v[2 * q] * (1.f / kTScale), v[2 * q + 1] * (1.f / kTScale), hi[q0], lo[q0]);
+            }
+            tmem_st8(slot + tlane + 64u + static_cast<uint32_t>(16 * h + 8 * qq), hi);
+            tmem_st8(slot + tlane + 96u + static_cast<uint32_t>(16 * h + 8 * qq), lo);
           }
-          tmem_st16(slot + tlane + 64u + static_cast<uint32_t>(16 * h), hi);
-          tmem_st16(slot + tlane + 96u + static_cast<uint32_t>(16 * h), lo);
         }
         G.eth[jc] = jc < rows_valid ? en * (1.f / (kTScale * kTScale)) : 0.f;
         tmem_st_wait();
       }
       tc_fence_before();
       gsync();
-      // ---- block energies (fixed order), DET, SEL inside the tile
-      const int nb = nv / f.B;
-      {
-        float v = G.eth[gt];
-        const int seg = rpb < 32 ? rpb : 32;
-        for (int off = seg >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (rpb <= 32) {
-          if ((gt & (seg - 1)) == 0 && gt / rpb < nb) G.Et[gt / rpb] = v;
-        } else {
-          if (lane == 0) G.red4[gw] = v;
-        }
-        gsync();
-        if (rpb > 32) {
-          if (gt < nb) {
-            float E = 0.f;
-            for (int w = 0; w < rpb / 32; ++w) E += G.red4[gt * (rpb / 32) + w];
-            G.Et[gt] = E;
-          }
-          gsync();
-        }
-        if (f.energy && gt < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + gt] = G.Et[gt];
-      }
       // ---- HX_b GEMM on all 128 rows with its A operand in tensor memory,
-      //      issued by the group's last warp while the first runs SEL and
-      //      the look-back (rows of unselected blocks are computed and
-      //      dropped); the issue waits for the tensor pipe's queue
+      //      issued by the group's last warp while the first runs the block
+      //      energies, SEL and the look-back (rows of unselected blocks are
+      //      computed and dropped); the issue waits for the tensor pipe's queue
       if (gt == kHxIssuer) {
         tc_fence_after();
         const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
@@ -468,11 +459,31 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         umma_commit(smem_u32(&hx_full[j]));
         hx_issued = true;
       }
+      // ---- block energies (fixed order), DET and SEL on the first warp: a
+      //      lane sums 4 rows, the lanes of a block combine by an xor tree
+      const int nb = nv / f.B;
       int cnt_w0 = 0;  // warp 0: selected blocks, known before the look-back
       if (gw == 0) {
+        const float4 e4 = reinterpret_cast<const float4 *>(G.eth)[lane];  // rows 4 lane .. 4 lane + 3
+        if (rpb >= 4) {  // rpb / 4 lanes per block, nb <= 32
+          const int seg = rpb >> 2;
+          float sv = (e4.x + e4.y) + (e4.z + e4.w);
+          for (int off = 1; off < seg; off <<= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+          const float Eb = __shfl_sync(0xffffffffu, sv, (lane * seg) & 31);
+          if (lane < nb) G.Et[lane] = Eb;
+        } else if (rpb == 2) {
+          G.Et[2 * lane] = e4.x + e4.y;
+          G.Et[2 * lane + 1] = e4.z + e4.w;
+        } else {
+          reinterpret_cast<float4 *>(G.Et)[lane] = e4;
+        }
+        __syncwarp();
+        const int64_t eb = f.energy ? f.eslot.slot(k) * f.F + s0 / f.B : 0;
         for (int b0 = 0; b0 < nb; b0 += 32) {
           const int b = b0 + lane;
-          const bool v = b < nb && G.Et[b] > p.tau;
+          const float E = b < nb ? G.Et[b] : 0.f;
+          if (f.energy && b < nb) f.energy[eb + b] = E;
+          const bool v = b < nb && E > p.tau;
           const unsigned msk = __ballot_sync(0xffffffffu, v);
           if (b < nb) G.rank[b] = v ? cnt_w0 + __popc(msk & ((1u << lane) - 1u)) : -1;
           cnt_w0 += __popc(msk);
