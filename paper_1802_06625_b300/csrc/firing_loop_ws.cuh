@@ -40,6 +40,7 @@ constexpr int kWsRawHalo = 64;                // halo samples staged (S <= 2)
 constexpr uint32_t kWsRawBytes = ((kWsRawHalo + kTTile) * 8 + 1023) / 1024 * 1024;  // 33 KB
 constexpr uint32_t kWsAOpBytes = 2u * (kTGroups + 2) * 1024;                       // 36 KB (hi | lo)
 constexpr uint32_t kWsMiscBytes = 8192;
+constexpr int kWsConvBatch = 3;               // converter pieces per thread in flight
 
 __host__ __device__ inline bool ws_loop_supported(int T) { return tc_shifts(T) <= 3; }
 // constants (FIR ns x hi/lo, HX hi/lo) | 2 raw stages | 2 operand buffers | misc
@@ -136,6 +137,31 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// Cold paths, kept out of line so the roles' loops stay compact in the
+// instruction caches.
+// A wait ran out (or the CTA stops): the first reports it and the run aborts.
+static __device__ __forceinline__ void ws_fail(const LoopParams &p, volatile int32_t *stop, uint32_t actor,
+                                            uint32_t where, uint64_t frame) {
+  if (!*stop) {
+    report_error(p.status, kDevTimeout, actor, where, frame);
+    atomicExch(&p.ls->abort, 1u);
+  }
+  *stop = 1;
+}
+// The frame's last tile was counted: publish its SINK record (c from the
+// last look-back word) and mark the frame slot ready.
+static __device__ __forceinline__ void ws_publish_frame(const LoopParams &p, int64_t fslot, int64_t rs, uint64_t seq,
+                                                     int tiles) {
+  p.done[fslot] = 0u;
+  __threadfence();  // every tile counted: their look-back words are visible
+  const uint64_t w = ld_acquire_u64(&p.look[fslot * tiles + tiles - 1]);
+  p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
+  p.rec_frame[rs] = static_cast<int64_t>(seq);
+  __threadfence();
+  st_release_u64(&p.ready[fslot], seq + 1);
+  __threadfence();
+}
+
 static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(TcLoopParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const LoopParams &p = tp.lp;
@@ -191,13 +217,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  auto fail = [&](uint32_t actor, uint32_t where, uint64_t frame) {
-    if (!*stop) {
-      report_error(p.status, kDevTimeout, actor, where, frame);
-      atomicExch(&p.ls->abort, 1u);
-    }
-    *stop = 1;
-  };
+  auto fail = [&](uint32_t actor, uint32_t where, uint64_t frame) { ws_fail(p, stop, actor, where, frame); };
 
   if (warp == 0) {
     // ================================================================ producer
@@ -345,33 +365,47 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         unsigned char *ahi = aop0 + b * kWsAOpBytes;
         unsigned char *alo = ahi + (kTGroups + S) * 1024;
         const int npieces = (kTGroups + S) * 64;
-        for (int q = ct; q < npieces; q += 128) {
-          const int row = q >> 3, pc = q & 7;
-          const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
-          float v[8];
-          if (kTR * j + 4 * pc < it.nv) {
-            // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read their
-            // halves in the other order, so each quarter-warp load covers all
-            // 32 banks once
-            const float4 *src =
-                reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
-            const int sw = (pc >> 2) & 1;
-            const float4 a0 = src[sw], a1 = src[sw ^ 1];
-            const float4 u0 = sw ? a1 : a0, u1 = sw ? a0 : a1;
-            v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
-            v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
-          } else {
+        // kWsConvBatch pieces per thread at a time: all their loads are
+        // issued before the first split, so the load latency is paid once
+        // per batch
+        for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
+          float4 u[kWsConvBatch][2];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+          for (int r = 0; r < kWsConvBatch; ++r) {
+            const int q = q0 + 128 * r;
+            const int row = q >> 3, pc = q & 7;
+            const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
+            if (q < npieces && kTR * j + 4 * pc < it.nv) {
+              // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read
+              // their halves in the other order, so each quarter-warp load
+              // covers all 32 banks once
+              const float4 *src =
+                  reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
+              const int sw = (pc >> 2) & 1;
+              const float4 a0 = src[sw], a1 = src[sw ^ 1];
+              u[r][0] = sw ? a1 : a0;
+              u[r][1] = sw ? a0 : a1;
+            } else {
+              u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+              u[r][1] = u[r][0];
+            }
           }
-          const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-          uint4 h4, l4;
-          split_pair(v[0], v[1], h4.x, l4.x);
-          split_pair(v[2], v[3], h4.y, l4.y);
-          split_pair(v[4], v[5], h4.z, l4.z);
-          split_pair(v[6], v[7], h4.w, l4.w);
-          *reinterpret_cast<uint4 *>(ahi + off) = h4;
-          *reinterpret_cast<uint4 *>(alo + off) = l4;
+#pragma unroll
+          for (int r = 0; r < kWsConvBatch; ++r) {
+            const int q = q0 + 128 * r;
+            if (q < npieces) {
+              const int row = q >> 3, pc = q & 7;
+              const uint32_t off =
+                  static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+              uint4 h4, l4;
+              split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
+              split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
+              split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
+              split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
+              *reinterpret_cast<uint4 *>(ahi + off) = h4;
+              *reinterpret_cast<uint4 *>(alo + off) = l4;
+            }
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -417,7 +451,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       //      (hi in columns 64-95, lo in 96-127, two FP16 per column)
       {
         float en = 0.f;
-#pragma unroll
+#pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           float v[32];
           tmem_ld32(slot + tlane + static_cast<uint32_t>(32 * h), v);
@@ -517,7 +551,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       tc_fence_after();
       if (cnt > 0) {
         const int rk = jc < rows_valid ? G.rank[jc / rpb] : -1;
-#pragma unroll
+#pragma unroll 1
         for (int hf = 0; hf < 2; ++hf) {
           float o[32];
           tmem_ld32(slot + tlane + static_cast<uint32_t>(hf * 32), o);
@@ -542,14 +576,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           __threadfence();
           const uint32_t old = atomicAdd(&p.done[fslot], 1u);
           if (old + 1u == static_cast<uint32_t>(f.tiles)) {
-            p.done[fslot] = 0u;
-            __threadfence();  // every tile counted: their look-back words are visible
-            const uint64_t w = ld_acquire_u64(&p.look[fslot * f.tiles + f.tiles - 1]);
-            p.rec_c[rs] = static_cast<int32_t>(static_cast<uint32_t>(w));
-            p.rec_frame[rs] = static_cast<int64_t>(seq);
-            __threadfence();
-            st_release_u64(&p.ready[fslot], seq + 1);
-            __threadfence();
+            ws_publish_frame(p, fslot, rs, seq, f.tiles);
             last = 1;
           }
         }
