@@ -323,15 +323,15 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           const uint32_t d = tmem + static_cast<uint32_t>(j * 128);
           for (int sh = 0; sh < ns; ++sh) {
             const uint32_t arow = static_cast<uint32_t>(S - sh) * 1024u;  // group -sh
-            const uint32_t pa[3] = {ah + arow, ah + arow, al + arow};
             const uint32_t bh = b0 + static_cast<uint32_t>(2 * sh) * kTOpBytes, bl = bh + kTOpBytes;
-            const uint32_t pb[3] = {bh, bl, bh};
-#pragma unroll
-            for (int pass = 0; pass < 3; ++pass)
+#pragma unroll 1
+            for (int pass = 0; pass < 3; ++pass) {
+              const uint32_t pa = (pass == 2 ? al : ah) + arow, pb = pass == 1 ? bl : bh;
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                umma_f16(d, umma_desc_sw128(pa[pass] + ks * 32), umma_desc_sw128(pb[pass] + ks * 32), kTIdescN64,
+                umma_f16(d, umma_desc_sw128(pa + ks * 32), umma_desc_sw128(pb + ks * 32), kTIdescN64,
                          (sh > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+            }
           }
           umma_commit(smem_u32(&fir_full[j]));
           umma_commit(smem_u32(&a_empty[b]));
@@ -482,14 +482,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       if (gt == kHxIssuer) {
         tc_fence_after();
         const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
-        const uint32_t pa[3] = {slot + 64u, slot + 64u, slot + 96u};
-        const uint32_t pb[3] = {bh, bl, bh};
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass)
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t pa = pass == 2 ? slot + 96u : slot + 64u, pb = pass == 1 ? bl : bh;
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            umma_f16_ts(slot, pa[pass] + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb[pass] + ks * 32),
-                        kTIdescN64, (pass > 0 || ks > 0) ? 1u : 0u);
+            umma_f16_ts(slot, pa + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb + ks * 32), kTIdescN64,
+                        (pass > 0 || ks > 0) ? 1u : 0u);
+        }
         umma_commit(smem_u32(&hx_full[j]));
         hx_issued = true;
       }
