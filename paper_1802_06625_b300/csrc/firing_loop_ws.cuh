@@ -41,6 +41,8 @@ constexpr uint32_t kWsRawBytes = ((kWsRawHalo + kTTile) * 8 + 1023) / 1024 * 102
 constexpr uint32_t kWsAOpBytes = 2u * (kTGroups + 2) * 1024;                       // 36 KB (hi | lo)
 constexpr uint32_t kWsMiscBytes = 8192;
 constexpr int kWsConvBatch = 3;               // converter pieces per thread in flight
+constexpr uint32_t kTIdescN128 = (1u << 4) | (static_cast<uint32_t>(128 >> 3) << 17) |
+                                 (static_cast<uint32_t>(kTRows >> 4) << 24);
 
 __host__ __device__ inline bool ws_loop_supported(int T) { return tc_shifts(T) <= 3; }
 // constants (FIR ns x hi/lo, HX hi/lo) | 2 raw stages | 2 operand buffers | misc
@@ -298,6 +300,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     }
   } else if (warp == 1) {
     // ================================================================ MMA
+    const uint64_t dbfir = umma_desc_sw128(smem_u32(bfir));
+    const uint64_t dlo = static_cast<uint64_t>((kTGroups + S) * 64);  // lo operand after hi
     int sentinels = 0;
     bool issued = false;
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
@@ -318,19 +322,20 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           mbar_arrive(smem_u32(&a_empty[b]));
         } else {
           tc_fence_after();
-          const unsigned char *a = aop0 + b * kWsAOpBytes;
-          const uint32_t ah = smem_u32(a), al = ah + (kTGroups + S) * 1024u, b0 = smem_u32(bfir);
+          // Per shift and K step, hi x [B_hi | B_lo] and lo x [B_hi | B_lo]
+          // as N = 128 GEMMs (the shift's hi and lo tap operands are adjacent,
+          // one 128-row operand): columns 0-63 collect hi x hi + lo x hi,
+          // 64-127 hi x lo + lo x lo.  Descriptors advance by adding the
+          // byte offset / 16 (all shared addresses are below 2^18 bytes).
+          const uint64_t dah = umma_desc_sw128(smem_u32(aop0 + b * kWsAOpBytes));
           const uint32_t d = tmem + static_cast<uint32_t>(j * 128);
           for (int sh = 0; sh < ns; ++sh) {
-            const uint32_t arow = static_cast<uint32_t>(S - sh) * 1024u;  // group -sh
-            const uint32_t bh = b0 + static_cast<uint32_t>(2 * sh) * kTOpBytes, bl = bh + kTOpBytes;
-#pragma unroll 1
-            for (int pass = 0; pass < 3; ++pass) {
-              const uint32_t pa = (pass == 2 ? al : ah) + arow, pb = pass == 1 ? bl : bh;
+            const uint64_t ds = dah + static_cast<uint64_t>((S - sh) * 64);  // row group -sh
+            const uint64_t db = dbfir + static_cast<uint64_t>(sh * (2 * kTOpBytes / 16));
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                umma_f16(d, umma_desc_sw128(pa + ks * 32), umma_desc_sw128(pb + ks * 32), kTIdescN64,
-                         (sh > 0 || pass > 0 || ks > 0) ? 1u : 0u);
+            for (int ks = 0; ks < 4; ++ks) {
+              umma_f16(d, ds + 2 * ks, db + 2 * ks, kTIdescN128, (sh > 0 || ks > 0) ? 1u : 0u);
+              umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN128, 1u);
             }
           }
           umma_commit(smem_u32(&fir_full[j]));
@@ -447,28 +452,28 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
       const int rows_valid = nv / kTR;
       const uint32_t slot = tmem + static_cast<uint32_t>(j * 128);
-      // ---- energies of the FIR rows; the rows split into the HX operand
-      //      (hi in columns 64-95, lo in 96-127, two FP16 per column)
+      // ---- FIR rows = columns 0-63 + columns 64-127; energies; each
+      //      16-column quarter split into the HX operand over the columns
+      //      64 + 16 qd .. + 15 it came from (hi in the first 8, lo in the
+      //      next 8, two FP16 per column)
       {
         float en = 0.f;
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          float v[32];
-          tmem_ld32(slot + tlane + static_cast<uint32_t>(32 * h), v);
+        for (int qd = 0; qd < 4; ++qd) {
+          float v[16], w[16];
+          tmem_ld16(slot + tlane + static_cast<uint32_t>(16 * qd), v);
+          tmem_ld16(slot + tlane + static_cast<uint32_t>(64 + 16 * qd), w);
           tmem_ld_wait();
+          uint32_t hi[8], lo[8];
 #pragma unroll
-          for (int qq = 0; qq < 2; ++qq) {
-            uint32_t hi[8], lo[8];
-#pragma unroll
-            for (int q0 = 0; q0 < 8; ++q0) {
-              const int q = 8 * qq + q0;
-              en = fmaf(v[2 * q], v[2 * q], en);
-              en = fmaf(v[2 * q + 1], v[2 * q + 1], en);
-              split_pair(v[2 * q] * (1.f / kTScale), v[2 * q + 1] * (1.f / kTScale), hi[q0], lo[q0]);
-            }
-            tmem_st8(slot + tlane + 64u + static_cast<uint32_t>(16 * h + 8 * qq), hi);
-            tmem_st8(slot + tlane + 96u + static_cast<uint32_t>(16 * h + 8 * qq), lo);
+          for (int q = 0; q < 8; ++q) {
+            const float y0 = v[2 * q] + w[2 * q], y1 = v[2 * q + 1] + w[2 * q + 1];
+            en = fmaf(y0, y0, en);
+            en = fmaf(y1, y1, en);
+            split_pair(y0 * (1.f / kTScale), y1 * (1.f / kTScale), hi[q], lo[q]);
           }
+          tmem_st8(slot + tlane + static_cast<uint32_t>(64 + 16 * qd), hi);
+          tmem_st8(slot + tlane + static_cast<uint32_t>(72 + 16 * qd), lo);
         }
         G.eth[jc] = jc < rows_valid ? en * (1.f / (kTScale * kTScale)) : 0.f;
         tmem_st_wait();
@@ -484,10 +489,10 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         const uint32_t bh = smem_u32(bhx), bl = bh + kTOpBytes;
 #pragma unroll 1
         for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t pa = pass == 2 ? slot + 96u : slot + 64u, pb = pass == 1 ? bl : bh;
+          const uint32_t pa = slot + (pass == 2 ? 72u : 64u), pb = pass == 1 ? bl : bh;
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            umma_f16_ts(slot, pa + static_cast<uint32_t>(8 * ks), umma_desc_sw128(pb + ks * 32), kTIdescN64,
+            umma_f16_ts(slot, pa + static_cast<uint32_t>(16 * ks), umma_desc_sw128(pb + ks * 32), kTIdescN64,
                         (pass > 0 || ks > 0) ? 1u : 0u);
         }
         umma_commit(smem_u32(&hx_full[j]));
