@@ -1,10 +1,13 @@
 // Batched firing of many independent graph instances (prune_batch_*): one
 // frame of every instance per step, three launches over the whole batch,
-// optionally replayed as a captured CUDA graph.
+// optionally replayed as a captured CUDA graph.  The FIR runs on tensor
+// cores (4096-sample tiles) when every instance has T <= 129 and B divides
+// 4096 (PRUNE_BATCH_FIR=cuda_cores keeps it on CUDA cores).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -19,6 +22,7 @@ void prune_set_create_error(const std::string &m);  // prune_runtime.cu
 
 struct prune_batch {
   int32_t n = 0, B = 0, N = 0, TS = 0, tp_max = 8;
+  bool fir_tc = false;  // FIR on tensor cores
   int dev = 0, sms = 148;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -90,6 +94,7 @@ prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   bp.timeout_ns = 2000000000ull;
   bp.status = b->status;
   bp.hx_chunk = b->tuning.hx_chunk;
+  bp.fir_tc = b->fir_tc ? 1 : 0;
   cudaError_t e = batch_launch_step(bp, b->tp_max, b->sms, b->stream, b->tuning.hx_grid);
   if (e != cudaSuccess) return bfail(b, PRUNE_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return PRUNE_OK;
@@ -140,7 +145,11 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
   b->B = B;
   b->N = N;
   b->dev = dev;
-  b->TS = fir_tile_samples(B);
+  int t_max = 1;
+  for (int32_t i = 0; i < n; ++i) t_max = std::max(t_max, descs[i].T);
+  const char *fe = std::getenv("PRUNE_BATCH_FIR");
+  b->fir_tc = batch_fir_tc_supported(B, t_max) && !(fe && std::string(fe) == "cuda_cores");
+  b->TS = b->fir_tc ? kTTile : fir_tile_samples(B);
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   auto bail = [&](prune_status s) {
     prune_set_create_error(b->err);
@@ -157,7 +166,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
     return bail(PRUNE_ECUDA);
   }
   // layout: per-instance offsets in shared buffers
-  int64_t samples = 0, taps_n = 0, hist_n = 0, blocks = 0;
+  int64_t samples = 0, taps_n = 0, hist_n = 0, blocks = 0, fops_n = 0;
   std::vector<int32_t> hx_map;
   int64_t fir_count = 0;
   b->inst_h.resize(n);
@@ -184,6 +193,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
     taps_n += d.T;
     hist_n += 2 * std::max(d.T - 1, 1);
     blocks += d.F;
+    if (b->fir_tc) fops_n += static_cast<int64_t>(tc_fir_ops_elems(d.T));
   }
   b->total_samples = samples;
   if (fir_count > (int64_t{1} << 31) - 1) {
@@ -205,7 +215,9 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
       (s = balloc(b, &b->hx_map, hx_map.size())) || (s = balloc(b, &b->status, 4)))
     return bail(s);
   if (N == kTcNc && (s = balloc(b, &bops, static_cast<size_t>(n) * hx_tc_b_elems(N)))) return bail(s);
-  int64_t to = 0, ho = 0, bo = 0;
+  uint16_t *fops = nullptr;
+  if (b->fir_tc && (s = balloc(b, &fops, static_cast<size_t>(fops_n)))) return bail(s);
+  int64_t to = 0, ho = 0, bo = 0, fo = 0;
   bool ok = true;
   for (int32_t i = 0; i < n && ok; ++i) {
     const prune_graph_desc &d = descs[i];
@@ -224,6 +236,12 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
          cudaMemcpyAsync(const_cast<float2 *>(in.H), d.H, sizeof(float2) * N * N, cudaMemcpyHostToDevice,
                          b->stream) == cudaSuccess;
     if (ok && bops) ok = hx_tc_prepare_b(in.H, N, const_cast<uint16_t *>(in.bops), b->stream) == cudaSuccess;
+    if (ok && fops) {  // block-Toeplitz tap operands (split FP16, 2^8 scale)
+      in.fops = fops + fo;
+      tc_prepare_fir_kernel<<<dim3(64, tc_shifts(d.T)), 64, 0, b->stream>>>(in.taps, d.T, fops + fo);
+      ok = cudaGetLastError() == cudaSuccess;
+      fo += static_cast<int64_t>(tc_fir_ops_elems(d.T));
+    }
     to += d.T;
     ho += 2 * std::max(d.T - 1, 1);
     bo += d.F;
@@ -237,7 +255,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
                        b->stream) == cudaSuccess &&
        cudaMemcpyAsync(b->hx_map, hx_map.data(), sizeof(int32_t) * hx_map.size(), cudaMemcpyHostToDevice,
                        b->stream) == cudaSuccess;
-  ok = ok && batch_enable_smem(b->tp_max, B, N);
+  ok = ok && batch_enable_smem(b->tp_max, B, N, b->fir_tc);
   if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) {
     b->err = std::string("batch upload failed: ") + cudaGetErrorString(cudaGetLastError());
     return bail(PRUNE_ECUDA);

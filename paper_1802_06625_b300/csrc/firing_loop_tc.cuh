@@ -31,22 +31,9 @@
 // bounded; tensor memory is freed on every path.
 #pragma once
 #include "firing_loop.cuh"
-#include "hx_tc.cuh"
+#include "tc_common.cuh"
 
 namespace prune {
-
-constexpr int kTR = 32;                  // complex outputs per GEMM row
-constexpr int kTRows = 128;              // GEMM rows per tile (M)
-constexpr int kTTile = kTR * kTRows;     // 4096 outputs per tile
-constexpr int kTMaxShifts = 5;           // T <= 4 * 32 + 1
-constexpr int kTGroups = kTRows / 8;     // 8-row groups of one GEMM operand (16)
-constexpr int kTMaxPieces = (kTGroups + kTMaxShifts - 1) * 64 / 256;  // per thread (5)
-constexpr uint32_t kTOpBytes = 64 * 128; // one 64 x 64 FP16 operand (8 KB)
-constexpr uint32_t kTIdescN64 = (1u << 4) | (static_cast<uint32_t>(64 >> 3) << 17) |
-                                (static_cast<uint32_t>(kTRows >> 4) << 24);
-constexpr float kTScale = 256.f;
-
-__host__ __device__ inline int tc_shifts(int T) { return 1 + (T - 1 + kTR - 1) / kTR; }
 
 __host__ inline bool tc_loop_supported(int N, int B, int T) {
   return N == 32 && B % kTR == 0 && B <= kTTile && kTTile % B == 0 && T <= (kTMaxShifts - 1) * kTR + 1;
@@ -64,47 +51,6 @@ __host__ __device__ inline size_t tc_pipe_bytes(int T) {
 __host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
   return 1024 + static_cast<size_t>(tc_shifts(T)) * 2 * kTOpBytes + 2 * kTOpBytes +
          static_cast<size_t>(tc_pipes(T)) * tc_pipe_bytes(T);
-}
-
-// Operand elements: ns shifts x {hi, lo} x 64 x 64 for FIR, {hi, lo} x 64 x 64 for HX.
-__host__ inline size_t tc_fir_ops_elems(int T) { return static_cast<size_t>(tc_shifts(T)) * 2 * 64 * 64; }
-__host__ inline size_t tc_hx_ops_elems() { return 2 * 64 * 64; }
-
-// Real form of a 32 x 32 complex matrix M (element getter) at row n, column k.
-__device__ __forceinline__ float real_form(float2 g, int n, int k) {
-  if ((n & 1) == 0) return (k & 1) == 0 ? g.x : -g.y;
-  return (k & 1) == 0 ? g.y : g.x;
-}
-
-__device__ __forceinline__ void store_split(uint16_t *ops, uint32_t half_elems, int n, int k, float v) {
-  v *= kTScale;
-  const __half hi = __float2half_rn(v);
-  const __half lo = __float2half_rn(v - __half2float(hi));
-  const uint32_t off = sw128_off(n, k, 64) >> 1;
-  ops[off] = __half_as_ushort(hi);
-  ops[half_elems + off] = __half_as_ushort(lo);
-}
-
-// FIR operands: shift s, real row n < 64 (output 2i+a), real column k < 64.
-static __global__ void tc_prepare_fir_kernel(const float2 *taps, int T, uint16_t *ops) {
-  const int s = blockIdx.y, n = blockIdx.x, k = threadIdx.x;
-  const int i = n >> 1, u = k >> 1;
-  const int t = i - u + kTR * s;
-  const float2 g = (t >= 0 && t < T) ? taps[t] : make_float2(0.f, 0.f);
-  store_split(ops + static_cast<size_t>(s) * 2 * 64 * 64, 64 * 64, n, k, real_form(g, n, k));
-}
-
-// HX operands: real form of H (32 x 32 complex).
-static __global__ void tc_prepare_hx_kernel(const float2 *H, uint16_t *ops) {
-  const int n = blockIdx.x, k = threadIdx.x;
-  store_split(ops, 64 * 64, n, k, real_form(H[(n >> 1) * kTR + (k >> 1)], n, k));
-}
-
-__host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const float2 *H, uint16_t *fir_ops,
-                                           uint16_t *hx_ops, cudaStream_t s) {
-  tc_prepare_fir_kernel<<<dim3(64, tc_shifts(T)), 64, 0, s>>>(taps, T, fir_ops);
-  tc_prepare_hx_kernel<<<64, 64, 0, s>>>(H, hx_ops);
-  return cudaGetLastError();
 }
 
 struct TcLoopParams {

@@ -64,19 +64,32 @@ def test_batch_matches_oracle_over_steps(G, N, graph):
 
 
 def test_batch_equals_single_graphs(G):
+    # Each instance alone: as a batch of one it runs the same kernels on the
+    # same data, so the records are bit-identical; as a single graph (actor
+    # path, FIR on CUDA cores) the control matches outside the guard band and
+    # the samples agree within the parity tolerance.
     B, N = 256, 64
     ws = _instances(B, N, seed=99, n=6)
     frames, recs = _run(G, B, N, ws, 2, graph=True)
     for i, w in enumerate(ws):
+        _, alone = _run(G, B, N, [w], 2, graph=True)
         g = G.Graph(w.F, B, w.T, N, w.tau, w.taps(), w.H(), C=3, out_frames=2)
         g.push(torch.stack([frames[k][i] for k in range(2)]).cuda())
         g.run(actors=True)
         single = g.pull()
         g.close()
+        x = np.stack([frames[k][i].numpy() for k in range(2)])
+        r = oracle.run(w.F, B, w.T, N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), x)
         for k in range(2):
-            assert single[k][1] == recs[k][i][1]
-            assert np.array_equal(single[k][2], recs[k][i][2])
-            assert np.array_equal(single[k][3], recs[k][i][3])   # same kernels arithmetic: bit-identical
+            assert alone[k][0][1] == recs[k][i][1]
+            assert np.array_equal(alone[k][0][2], recs[k][i][2])
+            assert np.array_equal(alone[k][0][3], recs[k][i][3])
+            _, c, idx, y = recs[k][i]
+            cs = single[k][1]
+            err, rms, nb = compare_frame(c, idx, y, cs, np.asarray(single[k][2])[:cs], single[k][3], r.energy[k],
+                                         np.float32(w.tau), B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (i, k, err / rms)
 
 
 def test_batched_workload_shapes_fire(G):
