@@ -5,15 +5,21 @@
 // so an instance's tap operands are loaded into shared memory once per run
 // of its tiles.
 //
-//   warps 0-7   per item: the raw tile and its halo arrive by bulk copy into
-//               a 2-stage ring (the copy of the next item is issued first);
-//               the tile becomes the split-FP16 chunk array; then the
-//               previous item's accumulator is read back: y = the two column
-//               halves added, scaled, written to the instance's FIR output
-//               frame, and the block energies (fixed order);
+//   warp 9      producer: reads each item's instance record once into a
+//               shared record, writes the delay token before an instance's
+//               first tile, and copies the raw tile and its halo into one of
+//               3 stages with bulk copies (up to 3 items ahead);
+//   warps 0-7   per item: the tile is read into registers and written back
+//               over the same stage as the split-FP16 chunk array (same size
+//               per sample), so the conversion of an item overlaps the
+//               GEMMs of the one before; then the previous item's
+//               accumulator is read back: y = the two column halves added,
+//               scaled, written to the instance's FIR output frame, and the
+//               block energies (fixed order);
 //   warp 8      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
 //               and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of two
-//               128-column TMEM accumulators.
+//               128-column TMEM accumulators, and frees the item's stage by
+//               a commit once they have read it.
 //
 // Hand-offs are mbarriers whose phase flips once per use.  Every wait is
 // bounded; warps 0-7 combine the outcome of each wait in a barrier with an
@@ -25,15 +31,19 @@
 
 namespace prune {
 
-constexpr int kBfThreads = 288;                 // 8 warps + the MMA warp
+constexpr int kBfThreads = 320;                 // 8 work warps, the MMA warp, the producer warp
 constexpr int kBfWork = 256;                    // threads of warps 0-7
 constexpr int kBfMaxShifts = 5;                 // T <= 129
 constexpr int kBfRawHalo = 128;                 // samples staged before a tile (S <= 4)
-constexpr uint32_t kBfRawBytes = (kBfRawHalo + kTTile) * 8;                     // 33 KB per stage
-constexpr uint32_t kBfAOpBytes = 2u * (kTGroups + kBfMaxShifts - 1) * 1024;      // 40 KB (hi | lo)
+constexpr int kBfStages = 3;
+constexpr uint32_t kBfRawBytes = (kBfRawHalo + kTTile) * 8;                     // 33 KB: raw tile + halo
+constexpr uint32_t kBfAOpBytes = 2u * (kTGroups + kBfMaxShifts - 1) * 1024;      // 40 KB: chunk array (hi | lo)
+constexpr uint32_t kBfStageBytes = kBfAOpBytes > kBfRawBytes ? kBfAOpBytes : kBfRawBytes;
 constexpr uint32_t kBfBOpBytes = kBfMaxShifts * 2 * kTOpBytes;                   // 80 KB
 constexpr uint32_t kBfMiscBytes = 2048;
-constexpr uint32_t kBfSmemBytes = 1024 + kBfBOpBytes + 2 * kBfRawBytes + kBfAOpBytes + kBfMiscBytes;
+constexpr int kBfMaxPieces = (kTGroups + kBfMaxShifts - 1) * 64 / 256;           // per thread (5)
+constexpr uint32_t kBfSmemBytes = 1024 + kBfBOpBytes + kBfStages * kBfStageBytes + kBfMiscBytes;
+static_assert(kBfStageBytes % 1024 == 0, "stages stay 1024-byte aligned");
 
 __host__ inline bool batch_fir_tc_supported(int B, int T_max) {
   return B % kTR == 0 && B <= kTTile && kTTile % B == 0 && tc_shifts(T_max) <= kBfMaxShifts;
@@ -51,23 +61,37 @@ __device__ __forceinline__ bool bf_bar_and(bool p) {
 }
 __device__ __forceinline__ void bf_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// Per-item record the producer leaves in shared memory with the stage.
+struct BfRec {
+  float2 *y;            // the instance's FIR output frame
+  float *energy;        // its block energies
+  float2 *hout;         // where its delay token after the frame goes (or null)
+  const uint16_t *fops; // its tap operands
+  int64_t s0, L;        // tile start, frame length (samples)
+  int32_t inst, nv, S, T;
+};
+
 static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(BatchParams bp) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~static_cast<uintptr_t>(1023));
   unsigned char *bops = base;                       // tap operands of the loaded instance (shift s: hi, lo)
-  unsigned char *raw0 = bops + kBfBOpBytes;         // 2 stages, sample s0 - kBfRawHalo at byte 0
-  unsigned char *aop = raw0 + 2 * kBfRawBytes;      // chunk array: hi (16 + S groups), then lo
-  unsigned char *misc = aop + kBfAOpBytes;
-  uint64_t *raw_full = reinterpret_cast<uint64_t *>(misc);  // [2]
-  uint64_t *a_full = raw_full + 2;                           // chunk array written
-  uint64_t *mma_done = a_full + 1;                           // [2] GEMMs into accumulator a completed
+  // stage k: the raw tile (sample s0 - kBfRawHalo at byte 0), then in place
+  // the chunk array: hi (16 + S groups of 1024 bytes), then lo
+  unsigned char *stage0 = bops + kBfBOpBytes;
+  unsigned char *misc = stage0 + kBfStages * kBfStageBytes;
+  uint64_t *raw_full = reinterpret_cast<uint64_t *>(misc);  // [3] raw tile landed (and its record)
+  uint64_t *a_full = raw_full + kBfStages;                   // [3] chunk array written
+  uint64_t *st_free = a_full + kBfStages;                    // [3] the GEMMs reading the stage completed
+  uint64_t *mma_done = st_free + kBfStages;                  // [2] GEMMs into accumulator a completed
   uint64_t *acc_empty = mma_done + 2;                        // [2] accumulator a read back
   uint64_t *fin = acc_empty + 2;                             // the issuer's last commit, at exit
+  uint64_t *b_full = fin + 1;                                // an instance's tap operands landed
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
-  volatile int32_t *s_shift = reinterpret_cast<volatile int32_t *>(misc + 136);  // S of the chunk array
-  float *eth = reinterpret_cast<float *>(misc + 256);        // [2][128] row energies per column half
+  volatile int32_t *s_shift = reinterpret_cast<volatile int32_t *>(misc + 136);  // [3] S of each stage's array
+  BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3]
+  float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * blockIdx.x / gridDim.x);
   const int i1 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * (blockIdx.x + 1) / gridDim.x);
@@ -75,7 +99,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   const int B = bp.B, rpb = B / kTR;
 
   if (tid == 0) {
-    for (int q = 0; q < 8; ++q) mbar_init(smem_u32(raw_full + q), 1);
+    for (int q = 0; q < 3 * kBfStages + 6; ++q) mbar_init(smem_u32(raw_full + q), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *stop = 0;
   }
@@ -95,12 +119,73 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     *stop = 1;
   };
 
-  if (warp == 8) {
+  if (warp == 9) {
+    // ================================================================ producer
+    int issued = 0;
+    for (int i = 0; i < n; ++i) {
+      const int st = i % kBfStages;
+      if (i >= kBfStages && !ws_wait(smem_u32(&st_free[st]), ((i / kBfStages) - 1) & 1, bp.timeout_ns, stop)) {
+        if (lane == 0) fail(23, 0);
+        break;
+      }
+      const int2 tm = bp.fir_map[i0 + i];
+      const BatchInst &in = bp.inst[tm.x];
+      const int T = in.T;
+      const int64_t L = static_cast<int64_t>(in.F) * B;
+      const int64_t s0 = static_cast<int64_t>(tm.y) * kTTile;
+      const int nv = static_cast<int>(min(static_cast<int64_t>(kTTile), L - s0));
+      const int S = tc_shifts(T) - 1;
+      const uint32_t halo = static_cast<uint32_t>(S) * kTR;     // staged halo samples
+      const uint32_t hoff = (kBfRawHalo - halo) * 8;             // halo starts here
+      const float2 *cur = in.x ? in.x : bp.x + in.x_off;
+      unsigned char *raw = stage0 + st * kBfStageBytes;
+      if (tm.y == 0 && halo > 0) {  // the delay token (or zeros) before the first tile
+        const float2 *hist = T <= 1 ? nullptr : in.hist ? in.hist + bp.parity * (T - 1) : in.hist_in;
+        for (int m = lane; m < static_cast<int>(halo); m += 32) {
+          const int dd = static_cast<int>(halo) - m;  // samples before s0
+          float2 v = make_float2(0.f, 0.f);
+          if (dd <= T - 1 && hist) v = hist[T - 1 - dd];
+          reinterpret_cast<float2 *>(raw + hoff)[m] = v;
+        }
+      }
+      if (lane == 0) {
+        BfRec r;
+        r.y = in.y;
+        r.energy = in.energy;
+        r.hout = T <= 1 ? nullptr : in.hist ? in.hist + (1 - bp.parity) * (T - 1) : in.hist_out;
+        r.fops = in.fops;
+        r.s0 = s0;
+        r.L = L;
+        r.inst = tm.x;
+        r.nv = nv;
+        r.S = S;
+        r.T = T;
+        rec[st] = r;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const uint32_t bytes = static_cast<uint32_t>(nv) * 8 + (tm.y > 0 ? halo * 8 : 0u);
+        mbar_arrive_tx(smem_u32(&raw_full[st]), bytes);
+        if (tm.y > 0)
+          bulk_g2s(smem_u32(raw + hoff), cur + s0 - halo, (halo + static_cast<uint32_t>(nv)) * 8,
+                   smem_u32(&raw_full[st]));
+        else
+          bulk_g2s(smem_u32(raw + kBfRawHalo * 8), cur, static_cast<uint32_t>(nv) * 8, smem_u32(&raw_full[st]));
+      }
+      ++issued;
+    }
+    // no copy may still write a stage when the CTA leaves
+    if (lane == 0)
+      for (int i = max(0, issued - kBfStages); i < issued; ++i)
+        mbar_wait_bounded(smem_u32(&raw_full[i % kBfStages]), (i / kBfStages) & 1, bp.timeout_ns);
+    __syncwarp();
+  } else if (warp == 8) {
     // ================================================================ MMA
     if (lane == 0) {
-      bool issued = false;
+      bool any = false;
       for (int i = 0; i < n; ++i) {
-        if (!ws_wait(smem_u32(a_full), i & 1, bp.timeout_ns, stop)) {
+        const int st = i % kBfStages;
+        if (!ws_wait(smem_u32(&a_full[st]), (i / kBfStages) & 1, bp.timeout_ns, stop)) {
           fail(20, 0);
           break;
         }
@@ -109,8 +194,8 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           break;
         }
         tc_fence_after();
-        const int S = *s_shift;
-        const uint64_t dah = umma_desc_sw128(smem_u32(aop));
+        const int S = s_shift[st];
+        const uint64_t dah = umma_desc_sw128(smem_u32(stage0 + st * kBfStageBytes));
         const uint64_t dlo = static_cast<uint64_t>((kTGroups + S) * 64);  // lo array after hi
         const uint64_t dbf = umma_desc_sw128(smem_u32(bops));
         const uint32_t d = tmem + static_cast<uint32_t>((i & 1) * 128);
@@ -124,9 +209,10 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           }
         }
         umma_commit(smem_u32(&mma_done[i & 1]));
-        issued = true;
+        umma_commit(smem_u32(&st_free[st]));
+        any = true;
       }
-      if (issued) {  // every GEMM this thread issued has completed
+      if (any) {  // every GEMM this thread issued has completed
         umma_commit(smem_u32(fin));
         mbar_wait_bounded(smem_u32(fin), 0u, bp.timeout_ns);
       }
@@ -135,53 +221,15 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   } else {
     // ================================================================ warps 0-7
     int loaded = -1;
-    auto geom = [&](int i, int2 &tm, int64_t &L, int64_t &s0, int &nv, int &S) {
-      tm = bp.fir_map[i0 + i];
-      const BatchInst &in = bp.inst[tm.x];
-      L = static_cast<int64_t>(in.F) * B;
-      s0 = static_cast<int64_t>(tm.y) * kTTile;
-      nv = static_cast<int>(min(static_cast<int64_t>(kTTile), L - s0));
-      S = tc_shifts(in.T) - 1;
-    };
-    // the raw tile of item i (and its halo) into stage st
-    auto load_raw = [&](int i, int st) {
-      int2 tm;
-      int64_t L, s0;
-      int nv, S;
-      geom(i, tm, L, s0, nv, S);
-      const BatchInst &in = bp.inst[tm.x];
-      const uint32_t halo = static_cast<uint32_t>(S) * kTR;     // staged halo samples
-      const uint32_t hoff = (kBfRawHalo - halo) * 8;             // halo starts here
-      const float2 *cur = in.x ? in.x : bp.x + in.x_off;
-      unsigned char *raw = raw0 + st * kBfRawBytes;
-      if (tm.y == 0 && halo > 0) {  // the delay token (or zeros) before the first tile: plain stores
-        const float2 *hist = in.T <= 1 ? nullptr : in.hist ? in.hist + bp.parity * (in.T - 1) : in.hist_in;
-        for (int m = tid; m < static_cast<int>(halo); m += kBfWork) {
-          const int dd = static_cast<int>(halo) - m;  // samples before s0
-          float2 v = make_float2(0.f, 0.f);
-          if (dd <= in.T - 1 && hist) v = hist[in.T - 1 - dd];
-          reinterpret_cast<float2 *>(raw + hoff)[m] = v;
-        }
-      }
-      if (tid == 0) {
-        const uint32_t bytes = static_cast<uint32_t>(nv) * 8 + (tm.y > 0 ? halo * 8 : 0u);
-        mbar_arrive_tx(smem_u32(&raw_full[st]), bytes);
-        if (tm.y > 0)
-          bulk_g2s(smem_u32(raw + hoff), cur + s0 - halo, (halo + static_cast<uint32_t>(nv)) * 8,
-                   smem_u32(&raw_full[st]));
-        else
-          bulk_g2s(smem_u32(raw + kBfRawHalo * 8), cur, static_cast<uint32_t>(nv) * 8, smem_u32(&raw_full[st]));
-      }
+    // bounded wait by every thread of warps 0-7, outcome combined
+    auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
+      const bool w = mbar_wait_bounded(smem_u32(mb), par, bp.timeout_ns);
+      return bf_bar_and(w && !*stop);
     };
     // accumulator of item ip back: y = (hi part + lo part) / 2^8 to the FIR
     // output frame, row energies, then the block energies in a fixed order
-    auto epilogue = [&](int ip) {
-      int2 tm;
-      int64_t L, s0;
-      int nv, S;
-      geom(ip, tm, L, s0, nv, S);
-      const BatchInst &in = bp.inst[tm.x];
-      const int rows_valid = nv / kTR;
+    auto epilogue = [&](int ip, const BfRec &r) {
+      const int rows_valid = r.nv / kTR;
       const int q4 = warp & 3, hf = warp >> 2;  // TMEM lane quarter, output half (16 complex)
       const int m = q4 * 32 + lane;             // GEMM row: output chunk jc
       const int jc = 16 * (m & 7) + (m >> 3);
@@ -199,100 +247,114 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       }
       eth[hf * 128 + jc] = jc < rows_valid ? e : 0.f;
       if (jc < rows_valid) {
-        float4 *dst = reinterpret_cast<float4 *>(in.y + s0 + kTR * jc + 16 * hf);
+        float4 *dst = reinterpret_cast<float4 *>(r.y + r.s0 + kTR * jc + 16 * hf);
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
       tc_fence_before();
       bf_bar();
       if (tid == 0) mbar_arrive(smem_u32(&acc_empty[ip & 1]));
-      const int nb = nv / B;
+      const int nb = r.nv / B;
       if (tid < nb) {
         float E = 0.f;
-        for (int r = 0; r < rpb; ++r) {
-          const int c = tid * rpb + r;
+        for (int k = 0; k < rpb; ++k) {
+          const int c = tid * rpb + k;
           E += eth[c] + eth[128 + c];
         }
-        in.energy[s0 / B + tid] = E;
+        r.energy[r.s0 / B + tid] = E;
       }
     };
 
-    if (n > 0) load_raw(0, 0);
     bool ok = true;
+    BfRec prev{};
+    uint32_t b_par = 0;
     for (int i = 0; i < n; ++i) {
-      const int st = i & 1;
-      if (i + 1 < n) load_raw(i + 1, st ^ 1);  // its stage was converted one item ago
-      bool w = mbar_wait_bounded(smem_u32(&raw_full[st]), (i >> 1) & 1, bp.timeout_ns);
-      if (w && i >= 1) w = mbar_wait_bounded(smem_u32(&mma_done[(i - 1) & 1]), ((i - 1) >> 1) & 1, bp.timeout_ns);
-      ok = bf_bar_and(w && !*stop);
+      const int st = i % kBfStages;
+      ok = wait_all(&raw_full[st], (i / kBfStages) & 1);
       if (!ok) break;
-      int2 tm;
-      int64_t L, s0;
-      int nv, S;
-      geom(i, tm, L, s0, nv, S);
-      const BatchInst &in = bp.inst[tm.x];
-      if (tm.x != loaded) {  // this instance's tap operands (no GEMM reads the old ones any more)
-        const uint4 *src = reinterpret_cast<const uint4 *>(in.fops);
-        uint4 *dst = reinterpret_cast<uint4 *>(bops);
-        for (int q = tid; q < static_cast<int>((S + 1) * 2 * kTOpBytes / 16); q += kBfWork) dst[q] = src[q];
-        loaded = tm.x;
-      }
-      // the tile as the permuted split-FP16 chunk array (the fused loops' layout)
-      const unsigned char *raw = raw0 + st * kBfRawBytes;
-      unsigned char *ahi = aop, *alo = aop + (kTGroups + S) * 1024;
-      const int npieces = (kTGroups + S) * 64;
-      for (int q0 = tid; q0 < npieces; q0 += 3 * kBfWork) {
-        float4 u[3][2];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int q = q0 + kBfWork * r;
-          const int row = q >> 3, pc = q & 7;
-          const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
-          if (q < npieces && kTR * j + 4 * pc < nv) {
-            // pieces 4-7 read their halves in the other order (bank-conflict free)
-            const float4 *src = reinterpret_cast<const float4 *>(raw + (kBfRawHalo + kTR * j + 4 * pc) * 8);
-            const int sw = (pc >> 2) & 1;
-            const float4 a0 = src[sw], a1 = src[sw ^ 1];
-            u[r][0] = sw ? a1 : a0;
-            u[r][1] = sw ? a0 : a1;
-          } else {
-            u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            u[r][1] = u[r][0];
-          }
+      const BfRec r = rec[st];
+      const int S = r.S, nv = r.nv;
+      bool prev_done = i == 0;  // the GEMMs of item i-1 have completed
+      const bool reload = r.inst != loaded;
+      if (reload) {  // this instance's tap operands by bulk copy, once no GEMM reads the old ones
+        if (!prev_done) {
+          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
+          if (!ok) break;
+          prev_done = true;
         }
+        if (tid == 0) {
+          mbar_arrive_tx(smem_u32(b_full), static_cast<uint32_t>(S + 1) * 2 * kTOpBytes);
+          for (int sh = 0; sh <= S; ++sh)
+            bulk_g2s(smem_u32(bops + sh * 2 * kTOpBytes), r.fops + static_cast<size_t>(sh) * 2 * 64 * 64,
+                     2 * kTOpBytes, smem_u32(b_full));
+        }
+        loaded = r.inst;
+      }
+      // the tile as the permuted split-FP16 chunk array (the fused loops'
+      // layout), written over the raw tile once every thread has read it
+      unsigned char *stg = stage0 + st * kBfStageBytes;
+      const int npieces = (kTGroups + S) * 64;
+      float4 u[kBfMaxPieces][2];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int q = q0 + kBfWork * r;
-          if (q < npieces) {
-            const int row = q >> 3, pc = q & 7;
-            const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-            uint4 h4, l4;
-            split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
-            split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
-            split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
-            split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
-            *reinterpret_cast<uint4 *>(ahi + off) = h4;
-            *reinterpret_cast<uint4 *>(alo + off) = l4;
-          }
+      for (int k = 0; k < kBfMaxPieces; ++k) {
+        const int q = tid + kBfWork * k;
+        const int row = q >> 3, pc = q & 7;
+        const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
+        if (q < npieces && kTR * j + 4 * pc < nv) {
+          // pieces 4-7 read their halves in the other order (bank-conflict free)
+          const float4 *src = reinterpret_cast<const float4 *>(stg + (kBfRawHalo + kTR * j + 4 * pc) * 8);
+          const int sw = (pc >> 2) & 1;
+          const float4 a0 = src[sw], a1 = src[sw ^ 1];
+          u[k][0] = sw ? a1 : a0;
+          u[k][1] = sw ? a0 : a1;
+        } else {
+          u[k][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+          u[k][1] = u[k][0];
         }
       }
       // the delay token after the frame: its last T-1 input samples
-      if (in.T > 1 && s0 + nv == L) {
-        float2 *hout = in.hist ? in.hist + (1 - bp.parity) * (in.T - 1) : in.hist_out;
-        if (hout)
-          for (int m = tid; m < in.T - 1; m += kBfWork)
-            hout[m] = reinterpret_cast<const float2 *>(raw)[kBfRawHalo + nv - (in.T - 1) + m];
+      if (r.hout && r.s0 + nv == r.L)
+        for (int m = tid; m < r.T - 1; m += kBfWork)
+          r.hout[m] = reinterpret_cast<const float2 *>(stg)[kBfRawHalo + nv - (r.T - 1) + m];
+      bf_bar();  // every raw sample of the stage has been read
+      unsigned char *ahi = stg, *alo = stg + (kTGroups + S) * 1024;
+#pragma unroll
+      for (int k = 0; k < kBfMaxPieces; ++k) {
+        const int q = tid + kBfWork * k;
+        if (q < npieces) {
+          const int row = q >> 3, pc = q & 7;
+          const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+          uint4 h4, l4;
+          split_pair(u[k][0].x, u[k][0].y, h4.x, l4.x);
+          split_pair(u[k][0].z, u[k][0].w, h4.y, l4.y);
+          split_pair(u[k][1].x, u[k][1].y, h4.z, l4.z);
+          split_pair(u[k][1].z, u[k][1].w, h4.w, l4.w);
+          *reinterpret_cast<uint4 *>(ahi + off) = h4;
+          *reinterpret_cast<uint4 *>(alo + off) = l4;
+        }
       }
-      if (tid == 0) *s_shift = S;
+      if (tid == 0) s_shift[st] = S;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bf_bar();
-      if (tid == 0) mbar_arrive(smem_u32(a_full));
-      if (i >= 1) epilogue(i - 1);  // overlaps the GEMMs of item i
+      if (reload) {  // the tap operands (copied while the tile was converted)
+        ok = wait_all(b_full, b_par);
+        b_par ^= 1u;
+        if (!ok) break;
+      } else {
+        bf_bar();
+      }
+      if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
+      if (i >= 1) {  // item i-1's accumulator, read back while item i's GEMMs run
+        if (!prev_done) {
+          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
+          if (!ok) break;
+        }
+        epilogue(i - 1, prev);
+      }
+      prev = r;
     }
     if (ok && n > 0) {
-      const bool w = mbar_wait_bounded(smem_u32(&mma_done[(n - 1) & 1]), ((n - 1) >> 1) & 1, bp.timeout_ns);
-      ok = bf_bar_and(w && !*stop);
-      if (ok) epilogue(n - 1);
+      ok = wait_all(&mma_done[(n - 1) & 1], ((n - 1) >> 1) & 1);
+      if (ok) epilogue(n - 1, prev);
     }
     if (!ok && tid == 0) fail(22, 0);
   }
