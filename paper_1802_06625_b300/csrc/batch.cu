@@ -34,6 +34,8 @@ struct prune_batch {
   std::vector<BatchInst> inst_h;
   int2 *fir_map = nullptr;
   int32_t *hx_map = nullptr;
+  int32_t *hx_pre = nullptr;   // N = 64: selected-tile prefix (written by DET/SEL each step)
+  uint32_t *hx_ctr = nullptr;
   prune_batch_tuning tuning{};  // launch shape in use (prune_batch_autotune)
   uint32_t *status = nullptr;
   int64_t steps = 0;
@@ -95,6 +97,8 @@ prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   bp.status = b->status;
   bp.hx_chunk = b->tuning.hx_chunk;
   bp.fir_tc = b->fir_tc ? 1 : 0;
+  bp.hx_pre = b->hx_pre;
+  bp.hx_ctr = b->hx_ctr;
   cudaError_t e = batch_launch_step(bp, b->tp_max, b->sms, b->stream, b->tuning.hx_grid);
   if (e != cudaSuccess) return bfail(b, PRUNE_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return PRUNE_OK;
@@ -214,7 +218,9 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
       (s = balloc(b, &b->inst_d, n)) || (s = balloc(b, &b->fir_map, fir_map.size())) ||
       (s = balloc(b, &b->hx_map, hx_map.size())) || (s = balloc(b, &b->status, 4)))
     return bail(s);
-  if (N == kTcNc && (s = balloc(b, &bops, static_cast<size_t>(n) * hx_tc_b_elems(N)))) return bail(s);
+  if (N == kTcNc && ((s = balloc(b, &bops, static_cast<size_t>(n) * hx_tc_b_elems(N))) ||
+                     (s = balloc(b, &b->hx_pre, static_cast<size_t>(n) + 1)) || (s = balloc(b, &b->hx_ctr, 1))))
+    return bail(s);
   uint16_t *fops = nullptr;
   if (b->fir_tc && (s = balloc(b, &fops, static_cast<size_t>(fops_n)))) return bail(s);
   int64_t to = 0, ho = 0, bo = 0, fo = 0;
@@ -249,6 +255,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
   ok = ok && cudaMemsetAsync(hist, 0, sizeof(float2) * hist_n, b->stream) == cudaSuccess &&
        cudaMemsetAsync(c, 0, sizeof(int32_t) * n, b->stream) == cudaSuccess &&
        cudaMemsetAsync(b->status, 0, sizeof(uint32_t) * 4, b->stream) == cudaSuccess &&
+       (!b->hx_ctr || cudaMemsetAsync(b->hx_ctr, 0, sizeof(uint32_t), b->stream) == cudaSuccess) &&
        cudaMemcpyAsync(b->inst_d, b->inst_h.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream) ==
            cudaSuccess &&
        cudaMemcpyAsync(b->fir_map, fir_map.data(), sizeof(int2) * fir_map.size(), cudaMemcpyHostToDevice,

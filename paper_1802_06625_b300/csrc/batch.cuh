@@ -86,6 +86,47 @@ static __global__ void __launch_bounds__(kDetThreads) batch_detsel_kernel(BatchP
     __syncthreads();
   }
   if (tid == 0) *in.c = running;
+  if (!bp.hx_pre) return;
+  // The last CTA to finish scans the instances' selected 128-row tiles into
+  // hx_pre, the work list of the tensor-core HX launch.
+  __shared__ int last;
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(bp.hx_ctr, 1u) == static_cast<uint32_t>(bp.n - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int RB = bp.B / kTcNc;
+  int carry = 0;
+  for (int i0 = 0; i0 < bp.n; i0 += kDetThreads) {
+    const int i = i0 + tid;
+    int t = 0;
+    if (i < bp.n) {
+      const BatchInst &ii = bp.inst[i];
+      t = (min(max(__ldcg(ii.c), 0), ii.F) * RB + kTcM - 1) / kTcM;
+    }
+    int x = t;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += o;
+    }
+    if (lane == 31) warp_off[warp] = x;
+    __syncthreads();
+    int before = carry, chunk = 0;
+    for (int w = 0; w < kDetThreads / 32; ++w) {
+      const int v = warp_off[w];
+      if (w < warp) before += v;
+      chunk += v;
+    }
+    if (i < bp.n) bp.hx_pre[i + 1] = before + x;
+    carry += chunk;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    bp.hx_pre[0] = 0;
+    *bp.hx_ctr = 0u;  // for the next step
+  }
 }
 
 // HX_b on CUDA cores for any N < 64: grid-stride over (instance, block j),
@@ -127,278 +168,273 @@ static __global__ void __launch_bounds__(kHxThreads) batch_hx_cuda_kernel(BatchP
 
 // HX_b on tcgen05 for N = 64: the single-instance tensor-core scheme (same
 // split, same GEMM order, so the results are bit-identical to it) over the
-// batch's work items (instance, 128-row tile of its selected rows), in a
-// two-stage pipeline: the selected rows of the next item are gathered into
-// the second operand buffer while the GEMMs of the current one run, and
-// the current item's output leaves its tensor-memory accumulator while the
-// next item's GEMMs run.  An instance's R operands are copied into shared
-// memory when the instance of the work item changes (after the GEMMs that
-// read the old ones have completed).
-// Balanced mode (up to kBatchHxMaxInst instances): every CTA scans the
-// instances' control tokens into a prefix of their selected tiles and fires
-// an equal contiguous share of those tiles, so the load is even whatever
-// the selections and R operands are reloaded only at instance boundaries.
-// Larger batches take the work items by chunks or grid stride.
-constexpr int kBatchHxMaxInst = 4096;
-constexpr uint32_t kBatchHxSmemBytes = 6 * kTcOpBytes + 64 + 4 * (kBatchHxMaxInst + 1) + 1024;
-// 2 x A (hi, lo), B (hi, lo), misc, tile prefix
+// selected 128-row tiles of the batch.  DET/SEL left the prefix of the
+// instances' selected tiles in hx_pre; CTA c fires an equal contiguous
+// share of them, so the load is even whatever the selections, and an
+// instance's R operands are reloaded only at its boundaries.
+//   warp 9      producer: per tile, the selected blocks' rows (contiguous
+//               in the FIR output, B * 8 bytes a block) by bulk copies into
+//               one of 2 stages of 64 KB;
+//   warps 0-7   the rows, read into registers, written back over the stage
+//               as the split-FP16 A operand (same size); then the previous
+//               tile's accumulator is written to the compacted output;
+//   warp 8      issues the 24 GEMMs of a tile into one of two 128-column
+//               accumulators; their completion frees the stage.
+// Every wait is bounded; warps 0-7 combine wait outcomes in a barrier with
+// an AND reduction; the issuer commits once more and waits before tensor
+// memory is freed.
+constexpr int kBhxThreads = 320;
+constexpr uint32_t kBhxStageBytes = 2 * kTcOpBytes;                      // 64 KB: 128 rows x 512 bytes
+constexpr uint32_t kBatchHxSmemBytes = 2 * kTcOpBytes + 2 * kBhxStageBytes + 1024 + 1024;  // B, stages, misc, align
 
-struct BatchHxItem {
-  int w, ii, tau, rows;  // w < 0: none
+struct BhxRec {
+  float2 *out;        // the tile's first output row
+  int32_t inst, nrows, pad0, pad1;
 };
 
-static __global__ void __launch_bounds__(kTcThreads, 1) batch_hx_tc_kernel(BatchParams bp) {
+static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(BatchParams bp) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~static_cast<uintptr_t>(1023));
-  unsigned char *abuf = base;                                  // stage s: hi at s * 2 * kTcOpBytes, lo after
-  unsigned char *b_hi = base + 4 * kTcOpBytes, *b_lo = base + 5 * kTcOpBytes;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 6 * kTcOpBytes);  // [2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 6 * kTcOpBytes + 16);
-  int32_t *s_flag = reinterpret_cast<int32_t *>(base + 6 * kTcOpBytes + 20);
-  int32_t *wsum = reinterpret_cast<int32_t *>(base + 6 * kTcOpBytes + 24);  // [8]
-  int32_t *pre = reinterpret_cast<int32_t *>(base + 6 * kTcOpBytes + 64);   // [n + 1] selected tiles before i
+  unsigned char *b_hi = base, *b_lo = base + kTcOpBytes;
+  unsigned char *stage0 = base + 2 * kTcOpBytes;  // stage k: rows (fp32), then in place A hi | A lo
+  unsigned char *misc = stage0 + 2 * kBhxStageBytes;
+  uint64_t *raw_full = reinterpret_cast<uint64_t *>(misc);  // [2] rows landed (and the record)
+  uint64_t *a_full = raw_full + 2;                           // [2] A operand written
+  uint64_t *st_free = a_full + 2;                            // [2] the GEMMs reading the stage completed
+  uint64_t *mma_done = st_free + 2;                          // [2] GEMMs into accumulator a completed
+  uint64_t *acc_empty = mma_done + 2;                        // [2] accumulator a read back
+  uint64_t *fin = acc_empty + 2;                             // the issuer's last commit, at exit
+  uint64_t *b_full = fin + 1;                                // an instance's R operands landed
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
+  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
+  BhxRec *rec = reinterpret_cast<BhxRec *>(misc + 256);      // [2]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int RB = bp.B / kTcNc;
-  const bool balanced = bp.n <= kBatchHxMaxInst;
+  const int RB = bp.B / kTcNc;                                // rows per block
+  // this CTA's selected tiles [r0, r0 + cnt) of the step
+  const int total = __ldcg(&bp.hx_pre[bp.n]);
+  const int r0 = static_cast<int>(static_cast<int64_t>(total) * blockIdx.x / gridDim.x);
+  const int cnt = static_cast<int>(static_cast<int64_t>(total) * (blockIdx.x + 1) / gridDim.x) - r0;
+
   if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
+    for (int q = 0; q < 12; ++q) mbar_init(smem_u32(raw_full + q), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *s_flag = 0;
+    *stop = 0;
   }
-  if (warp == 0) {
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(256u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t ph[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  int loaded = -1;
-  const int w1 = bp.hx_chunk > 0 ? min((blockIdx.x + 1) * bp.hx_chunk, bp.hx_items) : bp.hx_items;
-  const int ws = bp.hx_chunk > 0 ? 1 : gridDim.x;
-  int wn = bp.hx_chunk > 0 ? blockIdx.x * bp.hx_chunk : blockIdx.x;
-  int64_t r_next = 0, r_end = 0;  // balanced mode: this CTA's selected tiles [r_next, r_end)
-  int ib = 0;                     //   and the instance of r_next
-  if (balanced) {
-    // inclusive block scan of the selected tiles per instance, 256 at a time
-    int carry = 0;
-    for (int i0 = 0; i0 < bp.n; i0 += kTcThreads) {
-      const int i = i0 + tid;
-      int t = 0;
-      if (i < bp.n) {
-        const BatchInst &in = bp.inst[i];
-        t = (min(max(*in.c, 0), in.F) * RB + kTcM - 1) / kTcM;
-      }
-      int x = t;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-      }
-      if (lane == 31) wsum[warp] = x;
-      __syncthreads();
-      int before = carry, chunk = 0;
-#pragma unroll
-      for (int w = 0; w < kTcThreads / 32; ++w) {
-        const int v = wsum[w];
-        if (w < warp) before += v;
-        chunk += v;
-      }
-      if (i < bp.n) pre[i + 1] = before + x;
-      carry += chunk;
-      __syncthreads();
-    }
-    if (tid == 0) pre[0] = 0;
-    __syncthreads();
-    const int64_t total = pre[bp.n];
-    r_next = total * blockIdx.x / gridDim.x;
-    r_end = total * (blockIdx.x + 1) / gridDim.x;
-    int lo = 0, hi = bp.n;  // the instance i with pre[i] <= r_next < pre[i + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pre[mid] <= r_next) lo = mid;
-      else hi = mid;
-    }
-    ib = lo;
-  }
-  // the next item with rows to fire (uniform: control tokens read on the device)
-  auto next_item = [&]() -> BatchHxItem {
-    if (balanced) {
-      if (r_next >= r_end) return BatchHxItem{-1, 0, 0, 0};
-      while (pre[ib + 1] <= r_next) ++ib;
-      const BatchInst &in = bp.inst[ib];
-      const BatchHxItem it{static_cast<int>(r_next), ib, static_cast<int>(r_next - pre[ib]),
-                           min(max(*in.c, 0), in.F) * RB};
-      ++r_next;
-      return it;
-    }
-    for (; wn < w1; wn += ws) {
-      const int ii = bp.hx_map[wn];
-      const BatchInst &in = bp.inst[ii];
-      const int tau = wn - in.hx_tile0;
-      const int ck = min(max(*in.c, 0), in.F);
-      const int rows = ck * RB;
-      if (tau * kTcM < rows) {
-        const BatchHxItem it{wn, ii, tau, rows};
-        wn += ws;
-        return it;
-      }
-    }
-    return BatchHxItem{-1, 0, 0, 0};
-  };
-  // wait for the GEMMs of stage st (all threads, bounded)
-  auto drain = [&](int st) -> bool {
-    if (!pending[st]) return true;
-    if (!mbar_wait_bounded(smem_u32(&mbar[st]), ph[st], bp.timeout_ns)) return false;
-    ph[st] ^= 1u;
-    pending[st] = false;
-    return true;
-  };
-  auto load_b = [&](int ii) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(bp.inst[ii].bops);
-    uint4 *dst = reinterpret_cast<uint4 *>(b_hi);
-    for (int q = tid; q < static_cast<int>(2 * kTcOpBytes / 16); q += kTcThreads) dst[q] = src[q];
-    loaded = ii;
-  };
-  // the selected rows of an item as the split-FP16 A operand of stage st:
-  // every load of the thread is issued before the first split
-  auto gather = [&](const BatchHxItem &it, int st) {
-    const BatchInst &in = bp.inst[it.ii];
-    unsigned char *a_hi = abuf + st * 2 * kTcOpBytes, *a_lo = a_hi + kTcOpBytes;
-    constexpr int kPer = kTcM * (kTcK / 8) / kTcThreads;  // 8 pieces of 8 floats
-    float4 u[kPer][2];
-#pragma unroll
-    for (int n = 0; n < kPer; ++n) {
-      const int q = tid + n * kTcThreads;
-      const int m = q >> 4, cc = q & 15;
-      const int gr = it.tau * kTcM + m;
-      u[n][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      u[n][1] = u[n][0];
-      if (gr < it.rows) {
-        const int j = gr / RB, r = gr % RB;
-        const int b = in.idx[j];
-        if (b >= 0 && b < in.F) {
-          const float4 *src =
-              reinterpret_cast<const float4 *>(in.y + static_cast<int64_t>(b) * bp.B + r * kTcNc) + cc * 2;
-          u[n][0] = __ldg(src);
-          u[n][1] = __ldg(src + 1);
-        }
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < kPer; ++n) {
-      const int q = tid + n * kTcThreads;
-      const int m = q >> 4, cc = q & 15;
-      const float v[8] = {u[n][0].x, u[n][0].y, u[n][0].z, u[n][0].w, u[n][1].x, u[n][1].y, u[n][1].z, u[n][1].w};
-      const uint32_t off = sw128_off(m, cc * 8, kTcM);
-      *reinterpret_cast<uint4 *>(a_hi + off) = split_pack(v, false);
-      *reinterpret_cast<uint4 *>(a_lo + off) = split_pack(v, true);
-    }
-  };
-  auto issue = [&](int st) {  // thread 0: 3 passes x 8 K steps into accumulator st
-    tc_fence_after();
-    const uint32_t ah = smem_u32(abuf + st * 2 * kTcOpBytes), al = ah + kTcOpBytes;
-    const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-    const uint32_t pa[3] = {ah, ah, al}, pb[3] = {bh, bl, bh};
-    const uint32_t d = tmem + static_cast<uint32_t>(st * 128);
-#pragma unroll
-    for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-      for (int ks = 0; ks < kTcK / 16; ++ks) {
-        const uint32_t koff = static_cast<uint32_t>((ks >> 2) * kTcM * 128 + (ks & 3) * 32);
-        const uint32_t kboff = static_cast<uint32_t>((ks >> 2) * kTcNg * 128 + (ks & 3) * 32);
-        umma_f16(d, umma_desc_sw128(pa[pass] + koff), umma_desc_sw128(pb[pass] + kboff), kTcIdesc,
-                 (pass > 0 || ks > 0) ? 1u : 0u);
-      }
-    umma_commit(smem_u32(&mbar[st]));
-  };
-  // the item's output rows are consecutive in the compacted output: stage
-  // them row-major in the free operand buffer of stage st (16-byte chunks
-  // XOR-swizzled by row, so the row-per-thread stores hit every bank once
-  // per quarter warp), then copy the tile out with coalesced stores
-  auto epilogue = [&](const BatchHxItem &it, int st) {
-    const BatchInst &in = bp.inst[it.ii];
-    unsigned char *stg = abuf + st * 2 * kTcOpBytes;  // 128 rows x 512 bytes
-    const int qd = warp & 3, hf = warp >> 2;
-    const int m = qd * 32 + lane;
-    float v[64];
-#pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4) {
-      float t[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(st * 128 + hf * 64 + c4 * 16), t);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) v[c4 * 16 + e] = t[e];
-    }
-    tmem_ld_wait();
-    const float sc = 1.f / kTcBScale;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int c = hf * 16 + e;  // 16-byte chunk of row m
-      *reinterpret_cast<float4 *>(stg + m * 512 + ((c ^ (m & 31)) << 4)) =
-          make_float4(v[4 * e] * sc, v[4 * e + 1] * sc, v[4 * e + 2] * sc, v[4 * e + 3] * sc);
-    }
-    __syncthreads();
-    const int nrows = min(kTcM, it.rows - it.tau * kTcM);
-    float4 *dst = reinterpret_cast<float4 *>(in.out + static_cast<int64_t>(it.tau) * kTcM * kTcNc);
-    for (int g = tid; g < nrows * 32; g += kTcThreads) {
-      const int mm = g >> 5, c = g & 31;
-      dst[g] = *reinterpret_cast<const float4 *>(stg + mm * 512 + ((c ^ (mm & 31)) << 4));
-    }
+  auto fail = [&](uint32_t where) {
+    if (!*stop) report_error(bp.status, kDevTimeout, kActHx, where, 0);
+    *stop = 1;
   };
 
-  BatchHxItem cur = next_item();
-  int st = 0;
-  if (cur.w >= 0) {
-    load_b(cur.ii);
-    gather(cur, 0);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) issue(0);
-    pending[0] = true;
-  }
-  while (cur.w >= 0) {
-    const BatchHxItem nxt = next_item();
-    bool ok = true;
-    if (nxt.w >= 0) {
-      if (nxt.ii != loaded) {  // new R operands once the current GEMMs no longer read them
-        ok = drain(st);
-        __syncthreads();
-        if (ok) load_b(nxt.ii);
+  if (warp == 9) {
+    // ================================================================ producer
+    int ib = 0;  // instance of tile r: hx_pre[ib] <= r < hx_pre[ib + 1]
+    if (cnt > 0) {
+      int lo = 0, hi = bp.n;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldcg(&bp.hx_pre[mid]) <= r0) lo = mid;
+        else hi = mid;
       }
-      if (ok) gather(nxt, st ^ 1);
+      ib = lo;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ok) ok = drain(st);
-    if (!ok) {
-      if (tid == 0) report_error(bp.status, kDevTimeout, kActHx, 7, static_cast<uint64_t>(cur.ii));
-      *s_flag = 1;
+    int issued = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const int st = i & 1;
+      if (i >= 2 && !ws_wait(smem_u32(&st_free[st]), ((i >> 1) - 1) & 1, bp.timeout_ns, stop)) {
+        if (lane == 0) fail(24);
+        break;
+      }
+      const int r = r0 + i;
+      while (__ldcg(&bp.hx_pre[ib + 1]) <= r) ++ib;
+      const BatchInst &in = bp.inst[ib];
+      const int tau = r - __ldcg(&bp.hx_pre[ib]);
+      const int rows = min(max(__ldcg(in.c), 0), in.F) * RB;
+      const int nrows = min(kTcM, rows - tau * kTcM);
+      const int nblk = nrows / RB, j0 = tau * kTcM / RB;
+      unsigned char *stg = stage0 + st * kBhxStageBytes;
+      if (lane == 0) {
+        rec[st] = BhxRec{in.out + static_cast<int64_t>(tau) * kTcM * kTcNc, ib, nrows, 0, 0};
+        mbar_arrive_tx(smem_u32(&raw_full[st]), static_cast<uint32_t>(nblk) * bp.B * 8);
+      }
+      __syncwarp();
+      for (int q = lane; q < nblk; q += 32) {  // block j0 + q: RB rows of the FIR output
+        const int b = min(max(in.idx[j0 + q], 0), in.F - 1);
+        bulk_g2s(smem_u32(stg + static_cast<uint32_t>(q) * bp.B * 8), in.y + static_cast<int64_t>(b) * bp.B,
+                 static_cast<uint32_t>(bp.B) * 8, smem_u32(&raw_full[st]));
+      }
+      ++issued;
     }
-    tc_fence_before();
-    __syncthreads();
-    if (*s_flag) break;
-    if (nxt.w >= 0) {
-      if (tid == 0) issue(st ^ 1);
-      pending[st ^ 1] = true;
+    // no copy may still write a stage when the CTA leaves
+    if (lane == 0)
+      for (int i = max(0, issued - 2); i < issued; ++i)
+        mbar_wait_bounded(smem_u32(&raw_full[i & 1]), (i >> 1) & 1, bp.timeout_ns);
+    __syncwarp();
+  } else if (warp == 8) {
+    // ================================================================ MMA
+    if (lane == 0) {
+      bool any = false;
+      for (int i = 0; i < cnt; ++i) {
+        const int st = i & 1;
+        if (!ws_wait(smem_u32(&a_full[st]), (i >> 1) & 1, bp.timeout_ns, stop)) {
+          fail(25);
+          break;
+        }
+        if (i >= 2 && !ws_wait(smem_u32(&acc_empty[st]), ((i >> 1) - 1) & 1, bp.timeout_ns, stop)) {
+          fail(26);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ah = smem_u32(stage0 + st * kBhxStageBytes), al = ah + kTcOpBytes;
+        const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        const uint32_t d = tmem + static_cast<uint32_t>(st * 128);
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t pa = pass == 2 ? al : ah, pb = pass == 1 ? bl : bh;
+#pragma unroll
+          for (int ks = 0; ks < kTcK / 16; ++ks) {
+            const uint32_t koff = static_cast<uint32_t>((ks >> 2) * kTcM * 128 + (ks & 3) * 32);
+            const uint32_t kboff = static_cast<uint32_t>((ks >> 2) * kTcNg * 128 + (ks & 3) * 32);
+            umma_f16(d, umma_desc_sw128(pa + koff), umma_desc_sw128(pb + kboff), kTcIdesc,
+                     (pass > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(smem_u32(&mma_done[st]));
+        umma_commit(smem_u32(&st_free[st]));
+        any = true;
+      }
+      if (any) {  // every GEMM this thread issued has completed
+        umma_commit(smem_u32(fin));
+        mbar_wait_bounded(smem_u32(fin), 0u, bp.timeout_ns);
+      }
     }
-    tc_fence_after();
-    epilogue(cur, st);  // overlaps the next item's GEMMs
-    tc_fence_before();
-    __syncthreads();
-    cur = nxt;
-    st ^= 1;
+    __syncwarp();
+  } else {
+    // ================================================================ warps 0-7
+    int loaded = -1;
+    uint32_t b_par = 0;
+    auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
+      const bool w = mbar_wait_bounded(smem_u32(mb), par, bp.timeout_ns);
+      return bf_bar_and(w && !*stop);
+    };
+    auto epilogue = [&](int ip, const BhxRec &r) {  // accumulator of tile ip to the compacted output
+      const int a = ip & 1;
+      const int qd = warp & 3, hf = warp >> 2;
+      const int m = qd * 32 + lane;
+      float v[64];
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        float t[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(qd * 32) << 16) + static_cast<uint32_t>(a * 128 + hf * 64 + c4 * 16), t);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[c4 * 16 + e] = t[e];
+      }
+      tmem_ld_wait();
+      if (m < r.nrows) {
+        float4 *dst = reinterpret_cast<float4 *>(r.out + static_cast<int64_t>(m) * kTcNc + hf * 32);
+        const float sc = 1.f / kTcBScale;
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          dst[e] = make_float4(v[4 * e] * sc, v[4 * e + 1] * sc, v[4 * e + 2] * sc, v[4 * e + 3] * sc);
+      }
+      tc_fence_before();
+      bf_bar();
+      if (tid == 0) mbar_arrive(smem_u32(&acc_empty[a]));
+    };
+    bool ok = true;
+    BhxRec prev{};
+    for (int i = 0; i < cnt; ++i) {
+      const int st = i & 1;
+      ok = wait_all(&raw_full[st], (i >> 1) & 1);
+      if (!ok) break;
+      const BhxRec r = rec[st];
+      bool prev_done = i == 0;  // the GEMMs of tile i-1 have completed
+      const bool reload = r.inst != loaded;
+      if (reload) {  // this instance's R operands by bulk copy, once no GEMM reads the old ones
+        if (!prev_done) {
+          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
+          if (!ok) break;
+          prev_done = true;
+        }
+        if (tid == 0) {
+          const uint16_t *src = bp.inst[r.inst].bops;
+          mbar_arrive_tx(smem_u32(b_full), 2 * kTcOpBytes);
+          bulk_g2s(smem_u32(b_hi), src, kTcOpBytes, smem_u32(b_full));
+          bulk_g2s(smem_u32(b_lo), src + kTcOpBytes / 2, kTcOpBytes, smem_u32(b_full));
+        }
+        loaded = r.inst;
+      }
+      // the rows as the split-FP16 A operand, written over the stage once
+      // every thread has read its rows
+      unsigned char *stg = stage0 + st * kBhxStageBytes;
+      constexpr int kPer = kTcM * (kTcK / 8) / kTcThreads;  // 8 pieces of 8 floats
+      float4 u[kPer][2];
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int q = tid + k * kTcThreads;
+        const int m = q >> 4, cc = q & 15;
+        if (m < r.nrows) {
+          // pieces 4-7 of a quarter row read their halves in the other order (bank-conflict free)
+          const float4 *src = reinterpret_cast<const float4 *>(stg + m * 512 + cc * 32);
+          const int sw = (cc >> 2) & 1;
+          const float4 a0 = src[sw], a1 = src[sw ^ 1];
+          u[k][0] = sw ? a1 : a0;
+          u[k][1] = sw ? a0 : a1;
+        } else {
+          u[k][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+          u[k][1] = u[k][0];
+        }
+      }
+      bf_bar();
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int q = tid + k * kTcThreads;
+        const int m = q >> 4, cc = q & 15;
+        const float v[8] = {u[k][0].x, u[k][0].y, u[k][0].z, u[k][0].w, u[k][1].x, u[k][1].y, u[k][1].z, u[k][1].w};
+        const uint32_t off = sw128_off(m, cc * 8, kTcM);
+        *reinterpret_cast<uint4 *>(stg + off) = split_pack(v, false);
+        *reinterpret_cast<uint4 *>(stg + kTcOpBytes + off) = split_pack(v, true);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (reload) {
+        ok = wait_all(b_full, b_par);
+        b_par ^= 1u;
+        if (!ok) break;
+      } else {
+        bf_bar();
+      }
+      if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
+      if (i >= 1) {  // tile i-1's accumulator, read back while tile i's GEMMs run
+        if (!prev_done) {
+          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
+          if (!ok) break;
+        }
+        epilogue(i - 1, prev);
+      }
+      prev = r;
+    }
+    if (ok && cnt > 0) {
+      ok = wait_all(&mma_done[(cnt - 1) & 1], ((cnt - 1) >> 1) & 1);
+      if (ok) epilogue(cnt - 1, prev);
+    }
+    if (!ok && tid == 0) fail(27);
   }
-  drain(0);
-  drain(1);
+
+  // ---- leave: every role is done (or stopped); free tensor memory
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 8) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
   }
@@ -408,8 +444,9 @@ static __global__ void __launch_bounds__(kTcThreads, 1) batch_hx_tc_kernel(Batch
 // the request loop share them).  Dynamic shared memory above 48 KB must have
 // been enabled on these kernels in the calling translation unit
 // (batch_enable_smem).
-// hx_grid: CTAs of the HX launch (0: one wave, sms for tensor cores, 8 sms
-// for CUDA cores); with bp.hx_chunk > 0 the grid covers the items in chunks.
+// hx_grid: CTAs of the CUDA-core HX launch (0: one wave of 8 per SM); with
+// bp.hx_chunk > 0 the grid covers the items in chunks.  The tensor-core HX
+// (N = 64) needs bp.hx_pre and bp.hx_ctr (zero before the first step).
 static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, int sms, cudaStream_t stream,
                                             int hx_grid = 0) {
   if (bp.fir_tc)  // one persistent CTA per SM over equal shares of the tiles
@@ -420,9 +457,8 @@ static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, i
   const int wave = bp.N == kTcNc ? sms : sms * 8;
   const int want = bp.hx_chunk > 0 ? (bp.hx_items + bp.hx_chunk - 1) / bp.hx_chunk : (hx_grid > 0 ? hx_grid : wave);
   if (bp.N == kTcNc) {
-    // balanced mode: one persistent CTA per SM over the selected tiles
-    const int grid = bp.n <= kBatchHxMaxInst ? std::max(1, sms) : std::max(1, std::min(bp.hx_items, want));
-    batch_hx_tc_kernel<<<grid, kTcThreads, kBatchHxSmemBytes, stream>>>(bp);
+    // one persistent CTA per SM over equal shares of the selected tiles
+    batch_hx_tc_kernel<<<std::max(1, sms), kBhxThreads, kBatchHxSmemBytes, stream>>>(bp);
   } else {
     const int grid = std::max(1, std::min(bp.hx_items, want));
     const size_t smem = (static_cast<size_t>(bp.B) + static_cast<size_t>(bp.N) * bp.N) * sizeof(float2);

@@ -34,6 +34,8 @@ struct BatchParams {
   int32_t n, B, N, TS, parity, fir_tiles, hx_items;
   int32_t hx_chunk;         // > 0: CTA c fires items [c * hx_chunk, (c + 1) * hx_chunk); 0: grid-stride
   int32_t fir_tc;           // 1: FIR on tensor cores (TS = 4096, every instance has fops)
+  int32_t *hx_pre;          // N = 64: [n + 1] selected 128-row tiles before each instance (written by DET/SEL)
+  uint32_t *hx_ctr;         //   DET/SEL CTAs done (the last one writes hx_pre and resets it)
   uint64_t timeout_ns;
   uint32_t *status;
 };

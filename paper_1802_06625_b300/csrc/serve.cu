@@ -41,6 +41,8 @@ struct prune_server {
     BatchInst *inst_h = nullptr, *inst_d = nullptr;
     int2 *fir_h = nullptr, *fir_d = nullptr;
     int32_t *hx_h = nullptr, *hx_d = nullptr;
+    int32_t *pre_d = nullptr;   // tensor-core HX work list (written by DET/SEL)
+    uint32_t *ctr_d = nullptr;
     cudaEvent_t ev = nullptr;
   };
   std::vector<Stage> stage;
@@ -154,6 +156,8 @@ prune_status prune_server_destroy(prune_server *s) {
     cudaFree(t.inst_d);
     cudaFree(t.fir_d);
     cudaFree(t.hx_d);
+    cudaFree(t.pre_d);
+    cudaFree(t.ctr_d);
   }
   cudaFree(s->arena_base);
   cudaFree(s->status);
@@ -227,6 +231,9 @@ prune_status prune_server_create(const prune_server_desc *d, prune_server **out)
         cudaMalloc(&t.inst_d, sizeof(BatchInst) * s->max_entries) != cudaSuccess ||
         cudaMalloc(&t.fir_d, sizeof(int2) * s->max_fir) != cudaSuccess ||
         cudaMalloc(&t.hx_d, sizeof(int32_t) * s->max_hx) != cudaSuccess ||
+        cudaMalloc(&t.pre_d, sizeof(int32_t) * (s->max_entries + 1)) != cudaSuccess ||
+        cudaMalloc(&t.ctr_d, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemsetAsync(t.ctr_d, 0, sizeof(uint32_t), s->stream) != cudaSuccess ||
         cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(PRUNE_ENOMEM, "prune_server_create: step staging");
   }
@@ -369,6 +376,8 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
   bp.inst = t.inst_d;
   bp.fir_map = t.fir_d;
   bp.hx_map = t.hx_d;
+  bp.hx_pre = t.pre_d;
+  bp.hx_ctr = t.ctr_d;
   bp.x = nullptr;
   bp.n = n;
   bp.B = B;
