@@ -42,7 +42,8 @@ constexpr uint32_t kBfStageBytes = kBfAOpBytes > kBfRawBytes ? kBfAOpBytes : kBf
 constexpr uint32_t kBfBOpBytes = kBfMaxShifts * 2 * kTOpBytes;                   // 80 KB
 constexpr uint32_t kBfMiscBytes = 2048;
 constexpr int kBfMaxPieces = (kTGroups + kBfMaxShifts - 1) * 64 / 256;           // per thread (5)
-constexpr uint32_t kBfSmemBytes = 1024 + kBfBOpBytes + kBfStages * kBfStageBytes + kBfMiscBytes;
+constexpr uint32_t kBfXposeBytes = 8 * 2048;                                      // 2 KB per work warp
+constexpr uint32_t kBfSmemBytes = 1024 + kBfBOpBytes + kBfStages * kBfStageBytes + kBfMiscBytes + kBfXposeBytes;
 static_assert(kBfStageBytes % 1024 == 0, "stages stay 1024-byte aligned");
 
 __host__ inline bool batch_fir_tc_supported(int B, int T_max) {
@@ -92,6 +93,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   volatile int32_t *s_shift = reinterpret_cast<volatile int32_t *>(misc + 136);  // [3] S of each stage's array
   BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3]
   float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
+  float *xpose = reinterpret_cast<float *>(misc + kBfMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * blockIdx.x / gridDim.x);
   const int i1 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * (blockIdx.x + 1) / gridDim.x);
@@ -246,10 +248,26 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
         e = fmaf(v[q], v[q], e);
       }
       eth[hf * 128 + jc] = jc < rows_valid ? e : 0.f;
-      if (jc < rows_valid) {
-        float4 *dst = reinterpret_cast<float4 *>(r.y + r.s0 + kTR * jc + 16 * hf);
+      // y through a per-warp transpose: a store instruction then writes 8
+      // rows x 64 contiguous bytes instead of 32 rows x 16 bytes.  Chunk f
+      // of row x sits at chunk f ^ ((x >> 1) & 3): conflict-free both ways.
+      float *wx = xpose + warp * 512;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          *reinterpret_cast<float4 *>(wx + lane * 16 + ((f ^ ((lane >> 1) & 3)) << 2)) =
+              make_float4(v[16 * h2 + 4 * f], v[16 * h2 + 4 * f + 1], v[16 * h2 + 4 * f + 2], v[16 * h2 + 4 * f + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const int x = 8 * e4 + (lane >> 2), fq = lane & 3;  // row of the warp, 16-byte chunk
+          const float4 val = *reinterpret_cast<const float4 *>(wx + x * 16 + ((fq ^ ((x >> 1) & 3)) << 2));
+          const int mx = q4 * 32 + x, jx = 16 * (mx & 7) + (mx >> 3);
+          if (jx < rows_valid)
+            *reinterpret_cast<float4 *>(r.y + r.s0 + kTR * jx + 16 * hf + 2 * (4 * h2 + fq)) = val;
+        }
+        __syncwarp();
       }
       tc_fence_before();
       bf_bar();
