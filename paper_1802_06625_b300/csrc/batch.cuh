@@ -185,7 +185,9 @@ static __global__ void __launch_bounds__(kHxThreads) batch_hx_cuda_kernel(BatchP
 // memory is freed.
 constexpr int kBhxThreads = 320;
 constexpr uint32_t kBhxStageBytes = 2 * kTcOpBytes;                      // 64 KB: 128 rows x 512 bytes
-constexpr uint32_t kBatchHxSmemBytes = 2 * kTcOpBytes + 2 * kBhxStageBytes + 1024 + 1024;  // B, stages, misc, align
+constexpr uint32_t kBhxXposeBytes = 8 * 2048;                            // 2 KB per work warp
+constexpr uint32_t kBatchHxSmemBytes = 2 * kTcOpBytes + 2 * kBhxStageBytes + 1024 + kBhxXposeBytes + 1024;
+// B, stages, misc, transpose buffers, alignment
 
 struct BhxRec {
   float2 *out;        // the tile's first output row
@@ -209,6 +211,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
   BhxRec *rec = reinterpret_cast<BhxRec *>(misc + 256);      // [2]
+  float *xpose = reinterpret_cast<float *>(misc + 1024);     // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RB = bp.B / kTcNc;                                // rows per block
   // this CTA's selected tiles [r0, r0 + cnt) of the step
@@ -341,12 +344,30 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
         for (int e = 0; e < 16; ++e) v[c4 * 16 + e] = t[e];
       }
       tmem_ld_wait();
-      if (m < r.nrows) {
-        float4 *dst = reinterpret_cast<float4 *>(r.out + static_cast<int64_t>(m) * kTcNc + hf * 32);
-        const float sc = 1.f / kTcBScale;
+      // through a per-warp transpose, 64 bytes of each row per round: a
+      // store instruction writes 8 rows x 64 contiguous bytes.  Chunk f of
+      // row x sits at chunk f ^ ((x >> 1) & 3): conflict-free both ways.
+      (void)m;
+      float *wx = xpose + warp * 512;
+      const float sc = 1.f / kTcBScale;
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-          dst[e] = make_float4(v[4 * e] * sc, v[4 * e + 1] * sc, v[4 * e + 2] * sc, v[4 * e + 3] * sc);
+      for (int h4 = 0; h4 < 4; ++h4) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float *vv = v + 16 * h4 + 4 * f;
+          *reinterpret_cast<float4 *>(wx + lane * 16 + ((f ^ ((lane >> 1) & 3)) << 2)) =
+              make_float4(vv[0] * sc, vv[1] * sc, vv[2] * sc, vv[3] * sc);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const int x = 8 * e4 + (lane >> 2), fq = lane & 3;  // row of the warp, 16-byte chunk
+          const float4 val = *reinterpret_cast<const float4 *>(wx + x * 16 + ((fq ^ ((x >> 1) & 3)) << 2));
+          const int mx = qd * 32 + x;
+          if (mx < r.nrows)
+            *reinterpret_cast<float4 *>(r.out + static_cast<int64_t>(mx) * kTcNc + hf * 32 + 8 * h4 + 2 * fq) = val;
+        }
+        __syncwarp();
       }
       tc_fence_before();
       bf_bar();
