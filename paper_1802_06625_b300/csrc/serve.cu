@@ -11,6 +11,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,7 @@ void prune_set_create_error(const std::string &m);  // prune_runtime.cu
 struct prune_server {
   prune_server_desc d{};
   int dev = 0, sms = 148, tp_max = 8, TS = 0;
+  bool fir_tc = false;  // FIR on tensor cores (4096-sample tiles, per-stream tap operands)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   unsigned char *arena_base = nullptr;
@@ -59,6 +61,12 @@ struct prune_server {
 };
 
 namespace {
+
+// Bytes of a stream's tensor-core FIR tap operands (0 when the FIR runs on
+// CUDA cores).
+uint64_t fops_bytes_of(const prune_server *s, int32_t T) {
+  return s->fir_tc ? tc_fir_ops_elems(T) * sizeof(uint16_t) : 0;
+}
 
 prune_status sfail(prune_server *s, prune_status st, const std::string &m) {
   if (s) s->err = m;
@@ -186,7 +194,11 @@ prune_status prune_server_create(const prune_server_desc *d, prune_server **out)
   prune_server *s = new prune_server();
   s->d = *d;
   s->dev = dev;
-  s->TS = fir_tile_samples(d->B);
+  {
+    const char *fe = std::getenv("PRUNE_BATCH_FIR");
+    s->fir_tc = batch_fir_tc_supported(d->B, d->T_max) && !(fe && std::string(fe) == "cuda_cores");
+  }
+  s->TS = s->fir_tc ? kTTile : fir_tile_samples(d->B);
   s->tp_max = fir_taps_padded(d->T_max);
   s->bops_bytes = d->N == kTcNc ? hx_tc_b_elems(d->N) * sizeof(uint16_t) : 0;
   cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -237,7 +249,7 @@ prune_status prune_server_create(const prune_server_desc *d, prune_server **out)
         cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming) != cudaSuccess)
       return bail(PRUNE_ENOMEM, "prune_server_create: step staging");
   }
-  if (!batch_enable_smem(s->tp_max, d->B, d->N) || cudaStreamSynchronize(s->stream) != cudaSuccess)
+  if (!batch_enable_smem(s->tp_max, d->B, d->N, s->fir_tc) || cudaStreamSynchronize(s->stream) != cudaSuccess)
     return bail(PRUNE_ECUDA, std::string("prune_server_create: ") + cudaGetErrorString(cudaGetLastError()));
   *out = s;
   return PRUNE_OK;
@@ -259,7 +271,8 @@ prune_status prune_server_open(prune_server *s, const prune_graph_desc *g, int64
     }
   if (slot < 0) return sfail(s, PRUNE_EAGAIN, "prune_server_open: every stream slot is taken");
   const int N = s->d.N;
-  const StreamLayout l = stream_layout(g->F, s->d.B, g->T, N, s->d.frames_per_step, s->d.ring, s->bops_bytes);
+  const StreamLayout l =
+      stream_layout(g->F, s->d.B, g->T, N, s->d.frames_per_step, s->d.ring, s->bops_bytes, fops_bytes_of(s, g->T));
   uint64_t off = 0;
   if (!s->arena.alloc(l.total, &off))
     return sfail(s, PRUNE_EAGAIN, "prune_server_open: HBM budget: the stream needs " + std::to_string(l.total) +
@@ -287,6 +300,11 @@ prune_status prune_server_open(prune_server *s, const prune_graph_desc *g, int64
             cudaMemsetAsync(at<int32_t>(s, ss, l.c), 0, sizeof(int32_t) * s->d.ring, s->stream) == cudaSuccess;
   if (ok && N == kTcNc)
     ok = hx_tc_prepare_b(at<float2>(s, ss, l.H), N, at<uint16_t>(s, ss, l.bops), s->stream) == cudaSuccess;
+  if (ok && s->fir_tc) {  // block-Toeplitz tap operands (split FP16, 2^8 scale)
+    tc_prepare_fir_kernel<<<dim3(64, tc_shifts(g->T)), 64, 0, s->stream>>>(at<float2>(s, ss, l.taps), g->T,
+                                                                            at<uint16_t>(s, ss, l.fops));
+    ok = cudaGetLastError() == cudaSuccess;
+  }
   if (!ok) {
     s->arena.release(off);
     ss = StreamState{};
@@ -337,7 +355,7 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
       rec.fired.emplace_back(p.stream, 0);
     }
     rec.fired.back().second++;
-    const StreamLayout l = stream_layout(ss.F, B, ss.T, N, fps, s->d.ring, s->bops_bytes);
+    const StreamLayout l = stream_layout(ss.F, B, ss.T, N, fps, s->d.ring, s->bops_bytes, fops_bytes_of(s, ss.T));
     const int64_t L = static_cast<int64_t>(ss.F) * B;
     const int64_t slot = p.frame % s->d.ring;
     BatchInst in{};
@@ -345,6 +363,7 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
     in.taps = at<float2>(s, ss, l.taps);
     in.H = at<float2>(s, ss, l.H);
     in.bops = N == kTcNc ? at<uint16_t>(s, ss, l.bops) : nullptr;
+    in.fops = s->fir_tc ? at<uint16_t>(s, ss, l.fops) : nullptr;
     in.hist = nullptr;
     float2 *hist = at<float2>(s, ss, l.hist);
     const int tm1 = std::max(ss.T - 1, 1);
@@ -376,6 +395,7 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
   bp.inst = t.inst_d;
   bp.fir_map = t.fir_d;
   bp.hx_map = t.hx_d;
+  bp.fir_tc = s->fir_tc ? 1 : 0;
   bp.hx_pre = t.pre_d;
   bp.hx_ctr = t.ctr_d;
   bp.x = nullptr;
@@ -446,7 +466,8 @@ prune_status prune_server_pull(prune_server *s, int64_t id, prune_frame_out *out
   if (ss->pulled >= ss->done) return sfail(s, PRUNE_EAGAIN, "prune_server_pull: no done frame waiting");
   const int64_t f = ss->pulled;
   if (mem != PRUNE_MEM_DISCARD) {
-    const StreamLayout l = stream_layout(ss->F, s->d.B, ss->T, s->d.N, s->d.frames_per_step, s->d.ring, s->bops_bytes);
+    const StreamLayout l = stream_layout(ss->F, s->d.B, ss->T, s->d.N, s->d.frames_per_step, s->d.ring, s->bops_bytes,
+                                         fops_bytes_of(s, ss->T));
     const int64_t slot = f % s->d.ring;
     int32_t c = 0;
     if (cudaMemcpy(&c, at<int32_t>(s, *ss, l.c) + slot, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -95,13 +95,13 @@ class Arena {
 // the frames it fires in one step, and the result ring of `ring` frames
 // (c, idx, compacted HX output).
 struct StreamLayout {
-  uint64_t taps, H, bops, hist, y, energy, c, idx, out, total;
+  uint64_t taps, H, bops, fops, hist, y, energy, c, idx, out, total;
 };
 
 inline uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
 inline StreamLayout stream_layout(int64_t F, int64_t B, int64_t T, int64_t N, int64_t fps, int64_t ring,
-                                  uint64_t bops_bytes) {
+                                  uint64_t bops_bytes, uint64_t fops_bytes = 0) {
   StreamLayout l{};
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) {
@@ -113,6 +113,7 @@ inline StreamLayout stream_layout(int64_t F, int64_t B, int64_t T, int64_t N, in
   l.taps = take(8 * static_cast<uint64_t>(T));
   l.H = take(8 * static_cast<uint64_t>(N) * N);
   l.bops = take(bops_bytes);
+  l.fops = take(fops_bytes);
   l.hist = take(8 * 2 * static_cast<uint64_t>(std::max<int64_t>(T - 1, 1)));
   l.y = take(8 * L * fps);
   l.energy = take(4 * static_cast<uint64_t>(F) * fps);

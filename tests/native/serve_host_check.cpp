@@ -72,10 +72,11 @@ static void layout() {
         for (int fps : {1, 4})
           for (int ring : {fps, 2 * fps + 1}) {
             const uint64_t bops = N == 64 ? 65536 : 0;
-            StreamLayout l = stream_layout(F, 512, T, N, fps, ring, bops);
+            const uint64_t fops = T <= 129 ? 16384ull * (1 + (T - 1 + 31) / 32) : 0;
+            StreamLayout l = stream_layout(F, 512, T, N, fps, ring, bops, fops);
             const uint64_t L = uint64_t(F) * 512;
             const std::vector<std::pair<uint64_t, uint64_t>> parts = {
-                {l.taps, 8ull * T}, {l.H, 8ull * N * N}, {l.bops, bops}, {l.hist, 16ull * (T > 1 ? T - 1 : 1)},
+                {l.taps, 8ull * T}, {l.H, 8ull * N * N}, {l.bops, bops}, {l.fops, fops}, {l.hist, 16ull * (T > 1 ? T - 1 : 1)},
                 {l.y, 8 * L * fps}, {l.energy, 4ull * F * fps}, {l.c, 4ull * ring}, {l.idx, 4ull * F * ring},
                 {l.out, 8 * L * ring}};
             for (size_t i = 0; i < parts.size(); ++i) {
