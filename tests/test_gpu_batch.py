@@ -155,3 +155,47 @@ def test_every_launch_shape_gives_identical_results_and_autotune_keeps_state(G, 
             a, r = at.pull(i), recs_ref[k][i]
             assert a[0] == r[0] and np.array_equal(a[2], r[2]) and np.array_equal(a[3], r[3])
     at.close()
+
+
+# The tensor-core batched FIR (B | 4096, T <= 129) on other block sizes: B = 64
+# (one HX row per block, T up to 65) and B = 2048 (two blocks per tile, five
+# tap shifts at T = 129), ragged last tiles, against the oracle over steps.
+@pytest.mark.parametrize("B,specs", [(64, [(3, 65), (70, 64), (1, 1), (40, 33), (129, 9)]),
+                                     (2048, [(5, 129), (2, 65), (7, 8), (1, 2)])])
+def test_tensor_core_batch_fir_block_sizes(G, B, specs):
+    N = 64
+    ws = [synth.PlainWorkload(f"s{i}", F=F, B=B, T=T, N=N, frames=3, tau=float((2 + i % 5) * B),
+                              seed=700 + B + i, p=0.3 + 0.1 * i) for i, (F, T) in enumerate(specs)]
+    steps = 3
+    frames, recs = _run(G, B, N, ws, steps, graph=False)
+    for i, w in enumerate(ws):
+        x = np.stack([frames[k][i].numpy() for k in range(steps)])
+        r = oracle.run(w.F, B, w.T, N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), x)
+        for k in range(steps):
+            frame, c, idx, y = recs[k][i]
+            err, rms, nb = compare_frame(c, idx, y, r.c[k], r.idx[k], r.y[k], r.energy[k], np.float32(w.tau), B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (B, i, k, err / rms)
+
+
+def test_batch_fir_on_tensor_and_cuda_cores_agree(G, monkeypatch):
+    # the same instances with the FIR on tensor cores (default) and on CUDA
+    # cores (PRUNE_BATCH_FIR=cuda_cores): control equal outside the guard
+    # band, samples within the parity tolerance, both against the oracle
+    B, N = 256, 64
+    ws = _instances(B, N, seed=77, n=8)
+    frames, recs_tc = _run(G, B, N, ws, 2, graph=True)
+    monkeypatch.setenv("PRUNE_BATCH_FIR", "cuda_cores")
+    _, recs_cc = _run(G, B, N, ws, 2, graph=True)
+    for i, w in enumerate(ws):
+        x = np.stack([frames[k][i].numpy() for k in range(2)])
+        r = oracle.run(w.F, B, w.T, N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), x)
+        for k in range(2):
+            _, c, idx, y = recs_tc[k][i]
+            _, cc, idxc, yc = recs_cc[k][i]
+            err, rms, nb = compare_frame(c, idx, y, cc, np.asarray(idxc)[:cc], yc, r.energy[k], np.float32(w.tau), B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (i, k, err / rms)
+            err, rms, nb = compare_frame(cc, idxc, yc, r.c[k], r.idx[k], r.y[k], r.energy[k], np.float32(w.tau), B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (i, k, err / rms)
