@@ -367,6 +367,17 @@ def run_batched(args, dev):
         bt.fire(x, graph=True)
     bt.sync()
     t_batched = (time.perf_counter() - t0) / args.steps
+    # bytes the step must move: FIR 8 B in and 8 B out per sample, energies,
+    # idx, and HX 8 B in and 8 B out per selected sample
+    sel_samples = sum(bt.pull(i)[1] for i in range(b.instances)) * b.B
+    blocks = sum(w.F for w in ws_)
+    step_bytes = 16.0 * samples + 16.0 * sel_samples + 8.0 * blocks
+    peaks = measured_peaks()
+    roof = {"bound": "hbm", "achieved": step_bytes / t_batched / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "peak_source": "measured" if not peaks.get("fallback") else "fallback",
+            "frac": step_bytes / t_batched / 1e9 / peaks["hbm_gbs"], "bytes_per_step": step_bytes,
+            "selected_fraction": sel_samples / float(samples),
+            "note": "whole step (three launches) against the HBM copy bandwidth"}
     bt.close()
 
     graphs = [Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=1, out_frames=1, device=dev.index) for w in ws_]
@@ -394,7 +405,7 @@ def run_batched(args, dev):
     return {"workload": b.name, "instances": b.instances, "samples_per_step": samples,
             "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
             "plain_Msamples_s": samples / t_plain / 1e6, "plain_ms_per_step": 1e3 * t_plain,
-            "speedup": t_plain / t_batched,
+            "speedup": t_plain / t_batched, "roofline": roof,
             "tuning": tuned, "candidates_ms": [round(c["ms"], 4) for c in candidates],
             "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
                       "graph with the autotuned launch shape, plain = one graph object per instance (push, run, "
