@@ -90,7 +90,7 @@ __global__ void dpd_hist_kernel(const float2 *x, int64_t period, int32_t K, int3
 // shared memory and the branch's FIR accumulates into the thread's 8
 // outputs; taps t >= T are zero, so NT >= T taps are computed.
 template <int NT>
-__global__ void __launch_bounds__(kDpdThreads) dpd_kernel(DpdParams p) {
+__global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
   constexpr int HW = NT - 1;                                   // halo slots of the window
   constexpr int kWin = (HW + kDpdTile) + ((HW + kDpdTile) >> 3) + 2;
   __shared__ __align__(16) float2 xs[kDpdTile];
@@ -119,7 +119,21 @@ __global__ void __launch_bounds__(kDpdThreads) dpd_kernel(DpdParams p) {
   for (int j = 0; j < kDpdSPT; ++j) acc[j] = make_float2(0.f, 0.f);
   const int ob = tid * kDpdSPT;
   __syncthreads();
+  // the thread's window elements i = tid + 256 q: psi_k carried across the
+  // branches, psi_{k+1} = psi_k |x| (|x| once per element)
+  float2 px[kDpdSPT];
+  float rx[kDpdSPT];
+#pragma unroll
+  for (int q = 0; q < kDpdSPT; ++q) {
+    const int i = tid + q * kDpdThreads;
+    px[q] = i < nv ? xs[i] : make_float2(0.f, 0.f);
+    rx[q] = sqrtf(px[q].x * px[q].x + px[q].y * px[q].y);
+  }
   for (int k = 0; k < p.K; ++k) {
+    if (k > 0) {
+#pragma unroll
+      for (int q = 0; q < kDpdSPT; ++q) px[q] = make_float2(px[q].x * rx[q], px[q].y * rx[q]);
+    }
     if (!((m >> k) & 1u)) continue;  // the same branch set for the whole CTA
     // halo: window slot w < HW holds psi_k at sample s0 - HW + w of the
     // branch's stream (zero where no tap reaches)
@@ -137,8 +151,8 @@ __global__ void __launch_bounds__(kDpdThreads) dpd_kernel(DpdParams p) {
       }
       win[pad_idx(tid)] = v;
     }
-    for (int i = tid; i < kDpdTile; i += kDpdThreads)
-      win[pad_idx(HW + i)] = i < nv ? dpd_psi(xs[i], k + 1) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < kDpdSPT; ++q) win[pad_idx(HW + tid + q * kDpdThreads)] = px[q];
     __syncthreads();
     float2 r[kDpdSPT + HW];  // window slots ob .. ob + 7 + HW
 #pragma unroll
