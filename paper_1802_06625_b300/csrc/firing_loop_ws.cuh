@@ -65,6 +65,13 @@ struct WsGroup {
   long long prefix;
 };
 
+// Eight scaled floats as one 32-byte global store (address 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(float *dst, const float *v, float sc) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(v[0] * sc), "f"(v[1] * sc),
+               "f"(v[2] * sc), "f"(v[3] * sc), "f"(v[4] * sc), "f"(v[5] * sc), "f"(v[6] * sc), "f"(v[7] * sc)
+               : "memory");
+}
+
 // Cold paths, kept out of line so the roles' loops stay compact in the
 // instruction caches.
 // A wait ran out (or the CTA stops): the first reports it and the run aborts.
@@ -487,13 +494,12 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           float o[32];
           tmem_ld32(slot + tlane + static_cast<uint32_t>(hf * 32), o);
           tmem_ld_wait();
-          if (rk >= 0) {
-            float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
-                                                     hf * 16);
+          if (rk >= 0) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
+            float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
+                                                   hf * 16);
             const float sc = 1.f / kTScale;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              dst[q] = make_float4(o[4 * q] * sc, o[4 * q + 1] * sc, o[4 * q + 2] * sc, o[4 * q + 3] * sc);
+            for (int q = 0; q < 4; ++q) st_global_v8(dst + 8 * q, o + 8 * q, sc);
           }
         }
       }
