@@ -65,13 +65,6 @@ struct WsGroup {
   long long prefix;
 };
 
-// Eight scaled floats as one 32-byte global store (address 32-byte aligned).
-__device__ __forceinline__ void st_global_v8(float *dst, const float *v, float sc) {
-  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(v[0] * sc), "f"(v[1] * sc),
-               "f"(v[2] * sc), "f"(v[3] * sc), "f"(v[4] * sc), "f"(v[5] * sc), "f"(v[6] * sc), "f"(v[7] * sc)
-               : "memory");
-}
-
 // Cold paths, kept out of line so the roles' loops stay compact in the
 // instruction caches.
 // A wait ran out (or the CTA stops): the first reports it and the run aborts.

@@ -144,4 +144,11 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// Eight scaled floats as one 32-byte global store (address 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(float *dst, const float *v, float sc) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(v[0] * sc), "f"(v[1] * sc),
+               "f"(v[2] * sc), "f"(v[3] * sc), "f"(v[4] * sc), "f"(v[5] * sc), "f"(v[6] * sc), "f"(v[7] * sc)
+               : "memory");
+}
+
 }  // namespace prune
