@@ -93,8 +93,12 @@ template <int NT>
 __global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
   constexpr int HW = NT - 1;                                   // halo slots of the window
   constexpr int kWin = (HW + kDpdTile) + ((HW + kDpdTile) >> 3) + 2;
-  __shared__ __align__(16) float2 xs[kDpdTile];
-  __shared__ __align__(16) float2 win[kWin];
+  __shared__ __align__(16) float2 wins[2][kWin];  // double buffered: one barrier per branch
+  // the input tile, read once into registers before the first branch; its
+  // space is the second window, first written after the first branch's
+  // barrier
+  float2 *xs = wins[1];
+  static_assert(kWin >= kDpdTile, "the input tile fits in a window buffer");
   __shared__ float2 hs[kDpdMaxK * NT];
   const int tid = threadIdx.x;
   const int pi = blockIdx.y, tile = blockIdx.x;
@@ -129,12 +133,15 @@ __global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
     px[q] = i < nv ? xs[i] : make_float2(0.f, 0.f);
     rx[q] = sqrtf(px[q].x * px[q].x + px[q].y * px[q].y);
   }
+  int wb = 0;  // window buffer of the next active branch
   for (int k = 0; k < p.K; ++k) {
     if (k > 0) {
 #pragma unroll
       for (int q = 0; q < kDpdSPT; ++q) px[q] = make_float2(px[q].x * rx[q], px[q].y * rx[q]);
     }
     if (!((m >> k) & 1u)) continue;  // the same branch set for the whole CTA
+    float2 *win = wins[wb];
+    wb ^= 1;
     // halo: window slot w < HW holds psi_k at sample s0 - HW + w of the
     // branch's stream (zero where no tap reaches)
     if (tid < HW) {
@@ -164,9 +171,14 @@ __global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
 #pragma unroll
       for (int j = 0; j < kDpdSPT; ++j) cmac(acc[j], ht, r[HW + j - t]);
     }
-    __syncthreads();  // the next branch rewrites the window
+    // the next active branch writes the other buffer; the one after it
+    // writes this one only after the next branch's barrier, by which time
+    // every thread has read this one
   }
-  // coalesced store through shared memory
+  // coalesced store through shared memory (a buffer no thread still reads
+  // once every thread has passed this barrier)
+  __syncthreads();
+  float2 *win = wins[0];
 #pragma unroll
   for (int j = 0; j < kDpdSPT; ++j) win[pad_idx(ob + j)] = acc[j];
   __syncthreads();
