@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "prune.h"
@@ -111,6 +112,15 @@ struct prune_graph {
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
   std::vector<cudaEvent_t> event_pool;
+  // Pulls copy out on their own stream after the run that fired the records
+  // (an event per run), so a pull overlaps the runs and pushes enqueued
+  // after it.  Pinned staging for the records' control words and status.
+  cudaStream_t pull_stream = nullptr;
+  std::deque<std::pair<int64_t, cudaEvent_t>> run_ends;  // (frames fired through the run, its end)
+  std::vector<cudaEvent_t> run_ev_pool;
+  int32_t *pull_c = nullptr;
+  int64_t *pull_frame = nullptr;
+  uint32_t *pull_status = nullptr;
   double kind_ms[8] = {};
   int64_t kind_n[8] = {};
   // host view of the FIFO heads/tails in frames
@@ -149,9 +159,8 @@ prune_status galloc(prune_graph *g, T **p, size_t count) {
   return PRUNE_OK;
 }
 
-prune_status check_device_status(prune_graph *g) {
-  uint32_t st[4] = {0, 0, 0, 0};
-  CU(g, cudaMemcpy(st, g->status, sizeof st, cudaMemcpyDeviceToHost));
+// The device status words (already copied to the host) as a status.
+prune_status status_words(prune_graph *g, const uint32_t *st) {
   if (st[0] == kDevOk) return PRUNE_OK;
   static const char *actors[] = {"SRC", "FIR", "DET", "SEL", "HX", "SINK"};
   static const char *codes[] = {"ok", "bounded wait gave up", "FIFO underflow", "FIFO overflow", "aborted",
@@ -162,6 +171,20 @@ prune_status check_device_status(prune_graph *g) {
   g->poisoned = true;
   g->poison_code = st[0] == kDevTimeout ? PRUNE_ETIMEOUT : PRUNE_EDEVICE;
   return fail(g, g->poison_code, buf);
+}
+
+prune_status check_device_status(prune_graph *g) {
+  uint32_t st[4] = {0, 0, 0, 0};
+  CU(g, cudaMemcpy(st, g->status, sizeof st, cudaMemcpyDeviceToHost));
+  return status_words(g, st);
+}
+
+// Run end events whose records are all pulled go back to their pool.
+void recycle_run_events(prune_graph *g) {
+  while (!g->run_ends.empty() && g->run_ends.front().first <= g->pulled) {
+    g->run_ev_pool.push_back(g->run_ends.front().second);
+    g->run_ends.pop_front();
+  }
 }
 
 prune_status sync_and_check(prune_graph *g) {
@@ -450,6 +473,15 @@ prune_status prune_graph_destroy(prune_graph *g) {
     for (void *p : g->allocs) cudaFree(p);
     for (auto &t : g->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : g->event_pool) cudaEventDestroy(e);
+    for (auto &r : g->run_ends) cudaEventDestroy(r.second);
+    for (auto e : g->run_ev_pool) cudaEventDestroy(e);
+    if (g->pull_stream) {
+      cudaStreamSynchronize(g->pull_stream);
+      cudaStreamDestroy(g->pull_stream);
+    }
+    cudaFreeHost(g->pull_c);
+    cudaFreeHost(g->pull_frame);
+    cudaFreeHost(g->pull_status);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   }
   delete g;
@@ -520,6 +552,13 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
       return bail(PRUNE_ECUDA);
     }
     g->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&g->pull_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void **>(&g->pull_c), sizeof(int32_t) * out_cap, 0) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void **>(&g->pull_frame), sizeof(int64_t) * out_cap, 0) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void **>(&g->pull_status), sizeof(uint32_t) * 4, 0) != cudaSuccess) {
+    g->err = "pull stream or staging allocation failed";
+    return bail(PRUNE_ECUDA);
   }
   const int64_t L = g->L;
   const int32_t T = desc->T, N = desc->N;
@@ -636,6 +675,15 @@ prune_status prune_run(prune_graph *g, int32_t max_frames, int32_t *n_fired, int
     if (s != PRUNE_OK) return s;
     g->fired += n;
     g->runs++;
+    cudaEvent_t ev = nullptr;
+    if (!g->run_ev_pool.empty()) {
+      ev = g->run_ev_pool.back();
+      g->run_ev_pool.pop_back();
+    } else {
+      CU(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    CU(g, cudaEventRecord(ev, g->stream));
+    g->run_ends.emplace_back(g->fired, ev);
   }
   if (n_fired) *n_fired = n;
   if (flags & PRUNE_RUN_SYNC) return sync_and_check(g);
@@ -664,34 +712,55 @@ prune_status prune_pull(prune_graph *g, prune_frame_out *outs, int32_t max, int3
     // Stream-ordered drop: later firings reuse the slots after this work.
     const int32_t cnt = static_cast<int32_t>(std::min<int64_t>(avail, max));
     g->pulled += cnt;
+    recycle_run_events(g);
     if (n) *n = cnt;
     return PRUNE_OK;
   }
-  prune_status s = sync_and_check(g);
-  if (s != PRUNE_OK) return s;
   const int32_t cnt = static_cast<int32_t>(std::min<int64_t>(avail, max));
+  const int64_t last = g->pulled + cnt;  // records [pulled, last)
+  // after the run that fired the last record, on the pull stream
+  cudaEvent_t ev = nullptr;
+  for (auto &r : g->run_ends)
+    if (r.first >= last) {
+      ev = r.second;
+      break;
+    }
+  if (!ev) return fail(g, PRUNE_EINVAL, "prune_pull: no run fired these records");
+  cudaStream_t ps = g->pull_stream;
+  CU(g, cudaStreamWaitEvent(ps, ev, 0));
+  const int64_t s0 = g->pulled % g->out_cap;
+  const int64_t n1 = std::min<int64_t>(cnt, g->out_cap - s0);  // the ring wraps after n1 records
+  CU(g, cudaMemcpyAsync(g->pull_c, g->rec_c + s0, sizeof(int32_t) * n1, cudaMemcpyDeviceToHost, ps));
+  CU(g, cudaMemcpyAsync(g->pull_frame, g->rec_frame + s0, sizeof(int64_t) * n1, cudaMemcpyDeviceToHost, ps));
+  if (cnt > n1) {
+    CU(g, cudaMemcpyAsync(g->pull_c + n1, g->rec_c, sizeof(int32_t) * (cnt - n1), cudaMemcpyDeviceToHost, ps));
+    CU(g, cudaMemcpyAsync(g->pull_frame + n1, g->rec_frame, sizeof(int64_t) * (cnt - n1), cudaMemcpyDeviceToHost, ps));
+  }
+  CU(g, cudaMemcpyAsync(g->pull_status, g->status, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, ps));
+  CU(g, cudaStreamSynchronize(ps));
+  {
+    const uint32_t st[4] = {g->pull_status[0], g->pull_status[1], g->pull_status[2], g->pull_status[3]};
+    const prune_status s = status_words(g, st);
+    if (s != PRUNE_OK) return s;
+  }
   const cudaMemcpyKind kind = mem == PRUNE_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   for (int32_t i = 0; i < cnt; ++i) {
     const int64_t slot = (g->pulled + i) % g->out_cap;
-    int32_t c = 0;
-    int64_t frame = 0;
-    if (outs || mem != PRUNE_MEM_DISCARD) {
-      CU(g, cudaMemcpy(&c, g->rec_c + slot, sizeof c, cudaMemcpyDeviceToHost));
-      CU(g, cudaMemcpy(&frame, g->rec_frame + slot, sizeof frame, cudaMemcpyDeviceToHost));
-    }
+    const int32_t c = g->pull_c[i];
     if (outs) {
-      outs[i].frame = frame;
+      outs[i].frame = g->pull_frame[i];
       outs[i].c = c;
       if (mem != PRUNE_MEM_DISCARD && c > 0) {
         if (!outs[i].idx || !outs[i].y) return fail(g, PRUNE_EINVAL, "prune_pull: idx and y buffers are required");
-        CU(g, cudaMemcpyAsync(outs[i].idx, g->rec_idx + slot * g->d.F, sizeof(int32_t) * c, kind, g->stream));
+        CU(g, cudaMemcpyAsync(outs[i].idx, g->rec_idx + slot * g->d.F, sizeof(int32_t) * c, kind, ps));
         CU(g, cudaMemcpyAsync(outs[i].y, g->rec_y + slot * g->L, sizeof(float2) * static_cast<size_t>(c) * g->d.B,
-                              kind, g->stream));
+                              kind, ps));
       }
     }
   }
-  CU(g, cudaStreamSynchronize(g->stream));
+  CU(g, cudaStreamSynchronize(ps));
   g->pulled += cnt;
+  recycle_run_events(g);
   if (n) *n = cnt;
   return PRUNE_OK;
 }
