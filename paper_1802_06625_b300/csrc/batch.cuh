@@ -260,11 +260,11 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
         break;
       }
       const int r = r0 + i;
-      while (__ldcg(&bp.hx_pre[ib + 1]) <= r) ++ib;
+      while (ib + 1 < bp.n && __ldcg(&bp.hx_pre[ib + 1]) <= r) ++ib;
       const BatchInst &in = bp.inst[ib];
       const int tau = r - __ldcg(&bp.hx_pre[ib]);
       const int rows = min(max(__ldcg(in.c), 0), in.F) * RB;
-      const int nrows = min(kTcM, rows - tau * kTcM);
+      const int nrows = max(0, min(kTcM, rows - tau * kTcM));  // 0 only if the prefix disagrees with c
       const int nblk = nrows / RB, j0 = tau * kTcM / RB;
       unsigned char *stg = stage0 + st * kBhxStageBytes;
       if (lane == 0) {
