@@ -226,3 +226,27 @@ def test_device_firing_rule_with_frames_present(G):
     recs = g.pull()
     g.close()
     check_against_oracle(w, x.numpy(), recs)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_pull_overlapping_later_pushes_and_runs(G, path):
+    # Chunk k is pushed and fired before chunk k-1 is pulled: a pull copies
+    # out (on the graph's pull stream) after the run that fired its records
+    # while later pushes and runs are queued; the result ring (5 slots)
+    # wraps inside pulls.
+    w = synth.PlainWorkload("t", F=64, B=256, T=16, N=16, frames=13, tau=1024.0, seed=91, p=0.3, C=6)
+    x = w.frames_tensor(0, 13)
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=6, out_frames=5)
+    recs, prev = [], None
+    for k in range(0, 13, 2):
+        m = min(2, 13 - k)
+        g.push(x[k:k + m])
+        assert g.run(actors=path == "actors", cuda_cores=path == "cuda_cores") == m
+        if prev is not None:
+            got = g.pull(prev)
+            assert len(got) == prev
+            recs += got
+        prev = m
+    recs += g.pull(prev)
+    g.close()
+    check_against_oracle(w, x.numpy(), recs)
