@@ -14,8 +14,9 @@
 //               per sample), so the conversion of an item overlaps the
 //               GEMMs of the one before; then the previous item's
 //               accumulator is read back: y = the two column halves added,
-//               scaled, written to the instance's FIR output frame, and the
-//               block energies (fixed order);
+//               scaled, written to the instance's FIR output frame through a
+//               per-warp shared-memory transpose (8 rows x 64 contiguous bytes
+//               per store instruction), and the block energies (fixed order);
 //   warp 8      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
 //               and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of two
 //               128-column TMEM accumulators, and frees the item's stage by
@@ -50,7 +51,8 @@ __host__ inline bool batch_fir_tc_supported(int B, int T_max) {
   return B % kTR == 0 && B <= kTTile && kTTile % B == 0 && tc_shifts(T_max) <= kBfMaxShifts;
 }
 
-// Barrier over warps 0-7 that also ANDs a predicate across them.
+// Barriers over warps 0-7, the work warps of this kernel and of the batched
+// HX kernel (the first also ANDs a predicate across them).
 __device__ __forceinline__ bool bf_bar_and(bool p) {
   uint32_t r;
   asm volatile(
