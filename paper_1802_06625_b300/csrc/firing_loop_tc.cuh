@@ -448,13 +448,11 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           for (int i = 0; i < 16; ++i) o[16 + i] = t16[i];
           tmem_ld_wait();
         }
-        if (m < cnt * rpb) {
-          float4 *dst = reinterpret_cast<float4 *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
-                                                   (m % rpb) * kTR + hf * 16);
-          const float sc = 1.f / kTScale;
+        if (m < cnt * rpb) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
+          float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
+                                                 (m % rpb) * kTR + hf * 16);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            dst[i] = make_float4(o[4 * i] * sc, o[4 * i + 1] * sc, o[4 * i + 2] * sc, o[4 * i + 3] * sc);
+          for (int i = 0; i < 4; ++i) st_global_v8(dst + 8 * i, o + 8 * i, 1.f / kTScale);
         }
       }
     }
