@@ -525,6 +525,42 @@ def run_serving(args, dev):
                       "the stream's last step complete"}
 
 
+def copy_ceiling(xh, yh, d2h_bytes, dev, reps=3):
+    """Plain pinned copies of one e2e step's bytes: the step's input host to
+    device on one stream while its output bytes go device to host on
+    another (the link is full duplex but the host side shares it).  The e2e
+    step time over this one is the share of the box's copy ceiling."""
+    xb = xh.view(torch.uint8).reshape(-1)
+    yb = yh.view(torch.uint8).reshape(-1)[:d2h_bytes]
+    din = torch.empty(xb.numel(), dtype=torch.uint8, device=dev)
+    dout = torch.empty(max(1, yb.numel()), dtype=torch.uint8, device=dev)[:yb.numel()]
+    si, so = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def both():
+        with torch.cuda.stream(si):
+            din.copy_(xb, non_blocking=True)
+        with torch.cuda.stream(so):
+            yb.copy_(dout, non_blocking=True)
+
+    def alone():
+        with torch.cuda.stream(si):
+            din.copy_(xb, non_blocking=True)
+
+    out = {}
+    for name, fn in (("s_per_step", both), ("h2d_alone_s", alone)):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        out[name] = (time.perf_counter() - t0) / reps
+    out["h2d_alone_GBs"] = xb.numel() / out.pop("h2d_alone_s") / 1e9
+    out["in_and_out_GBs"] = (xb.numel() + yb.numel()) / out["s_per_step"] / 1e9
+    del din, dout
+    return out
+
+
 def run_e2e(args, w, dev, stream, rank, ws):
     from paper_1802_06625_b300 import _lib
     from paper_1802_06625_b300.graph import Graph
@@ -579,9 +615,12 @@ def run_e2e(args, w, dev, stream, rank, ws):
     dt = max_over_ranks(time.perf_counter() - t0, ws, dev)
     g.close()
     samples = sum_over_ranks(float(args.steps * E * L), ws, dev)
+    d2h_step = d2h // args.steps
+    ceiling = copy_ceiling(xh, yh, d2h_step, dev)
+    ceiling["frac"] = ceiling["s_per_step"] / (dt / args.steps)
     return {"value": samples / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": E * L * 8,
-            "d2h_bytes_per_step": d2h // args.steps, "frames_per_step": E,
-            "chunk_frames": ch,
+            "d2h_bytes_per_step": d2h_step, "frames_per_step": E,
+            "chunk_frames": ch, "copy_ceiling": ceiling,
             "note": "pinned host frames pushed (H2D) and records pulled (D2H) through the C ABI, in chunks "
                     "pipelined so that a chunk's pull overlaps the next chunk's push"}
 

@@ -3,37 +3,42 @@
 // each with its own taps (1 <= T <= 129).  One persistent CTA per SM fires a
 // contiguous, equal share of the batch's (instance, 4096-sample tile) items,
 // so an instance's tap operands are loaded into shared memory once per run
-// of its tiles.
+// of its tiles.  Four roles run concurrently on different items:
 //
-//   warp 9      producer: reads each item's instance record once into a
-//               shared record, writes the delay token before an instance's
-//               first tile, and copies the raw tile and its halo into one of
-//               3 stages with bulk copies (up to 3 items ahead);
-//   warps 0-7   per item: the tile is read into registers and written back
-//               over the same stage as the split-FP16 chunk array (same size
-//               per sample), so the conversion of an item overlaps the
-//               GEMMs of the one before; then the previous item's
-//               accumulator is read back: y = the two column halves added,
-//               scaled, written to the instance's FIR output frame through a
-//               per-warp shared-memory transpose (8 rows x 64 contiguous bytes
-//               per store instruction), and the block energies (fixed order);
-//   warp 8      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
-//               and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of two
-//               128-column TMEM accumulators, and frees the item's stage by
-//               a commit once they have read it.
+//   warp 17      producer: reads each item's instance record once into a
+//                shared record, writes the delay token before an instance's
+//                first tile, and copies the raw tile and its halo into one of
+//                3 stages with bulk copies (up to 3 items ahead);
+//   warps 0-7    converter: the tile is read into registers and written back
+//                over the same stage as the split-FP16 chunk array (same size
+//                per sample); on a change of instance, its tap operands are
+//                copied in once the GEMMs of the item before have completed;
+//   warp 16      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
+//                and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of two
+//                128-column TMEM accumulators, hands the item's record on
+//                with the accumulator, and frees the stage by a commit once
+//                the GEMMs have read it;
+//   warps 8-15   read-back: y = the two column halves added, scaled, written
+//                to the instance's FIR output frame through a per-warp
+//                shared-memory transpose (8 rows x 64 contiguous bytes per
+//                store instruction), and the block energies (fixed order).
 //
-// Hand-offs are mbarriers whose phase flips once per use.  Every wait is
-// bounded; warps 0-7 combine the outcome of each wait in a barrier with an
-// AND reduction, so they leave together.  The issuing thread commits once
-// more to a barrier of its own and waits before tensor memory is freed.
+// Hand-offs are mbarriers whose phase flips once per use; each wait is on a
+// barrier that cannot run two phases ahead of its waiter, so the parity
+// names the use.  Every wait is bounded and also returns once the CTA's stop
+// flag is set; the converter and the read-back warps each combine the outcome
+// of a wait in a barrier with an AND reduction, so a group leaves together.
+// The issuing thread commits once more to a barrier of its own and waits
+// before tensor memory is freed.
 #pragma once
 #include "batch_types.cuh"
 #include "tc_common.cuh"
 
 namespace prune {
 
-constexpr int kBfThreads = 320;                 // 8 work warps, the MMA warp, the producer warp
-constexpr int kBfWork = 256;                    // threads of warps 0-7
+constexpr int kBfThreads = 576;                 // converter warps 0-7, read-back 8-15, MMA 16, producer 17
+constexpr int kBfWork = 256;                    // threads of one group of 8 warps
+constexpr int kBfMmaWarp = 16, kBfProdWarp = 17;
 constexpr int kBfMaxShifts = 5;                 // T <= 129
 constexpr int kBfRawHalo = 128;                 // samples staged before a tile (S <= 4)
 constexpr int kBfStages = 3;
@@ -42,27 +47,35 @@ constexpr uint32_t kBfAOpBytes = 2u * (kTGroups + kBfMaxShifts - 1) * 1024;     
 constexpr uint32_t kBfStageBytes = kBfAOpBytes > kBfRawBytes ? kBfAOpBytes : kBfRawBytes;
 constexpr uint32_t kBfBOpBytes = kBfMaxShifts * 2 * kTOpBytes;                   // 80 KB
 constexpr uint32_t kBfMiscBytes = 2048;
-constexpr int kBfMaxPieces = (kTGroups + kBfMaxShifts - 1) * 64 / 256;           // per thread (5)
-constexpr uint32_t kBfXposeBytes = 8 * 2048;                                      // 2 KB per work warp
+constexpr int kBfMaxPieces = (kTGroups + kBfMaxShifts - 1) * 64 / kBfWork;       // per converter thread (5)
+constexpr uint32_t kBfXposeBytes = 8 * 2048;                                      // 2 KB per read-back warp
 constexpr uint32_t kBfSmemBytes = 1024 + kBfBOpBytes + kBfStages * kBfStageBytes + kBfMiscBytes + kBfXposeBytes;
 static_assert(kBfStageBytes % 1024 == 0, "stages stay 1024-byte aligned");
+static_assert((kTGroups + kBfMaxShifts - 1) * 64 % kBfWork == 0, "converter pieces divide evenly");
 
 __host__ inline bool batch_fir_tc_supported(int B, int T_max) {
   return B % kTR == 0 && B <= kTTile && kTTile % B == 0 && tc_shifts(T_max) <= kBfMaxShifts;
 }
 
-// Barriers over warps 0-7, the work warps of this kernel and of the batched
-// HX kernel (the first also ANDs a predicate across them).
-__device__ __forceinline__ bool bf_bar_and(bool p) {
+// Barriers over one group of 8 warps (256 threads), named kId (the first
+// also ANDs a predicate across the group).
+template <int kId>
+__device__ __forceinline__ bool bar256_and(bool p) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n barrier.cta.red.and.pred b, 1, 256, a;\n selp.u32 %0, 1, 0, b;\n}"
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n barrier.cta.red.and.pred b, %2, 256, a;\n selp.u32 %0, 1, 0, b;\n}"
       : "=r"(r)
-      : "r"(p ? 1u : 0u)
+      : "r"(p ? 1u : 0u), "n"(kId)
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void bf_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+template <int kId>
+__device__ __forceinline__ void bar256() {
+  asm volatile("bar.sync %0, 256;" ::"n"(kId) : "memory");
+}
+// The work warps (0-7) of the batched HX kernel.
+__device__ __forceinline__ bool bf_bar_and(bool p) { return bar256_and<1>(p); }
+__device__ __forceinline__ void bf_bar() { bar256<1>(); }
 
 // Per-item record the producer leaves in shared memory with the stage.
 struct BfRec {
@@ -92,9 +105,9 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   uint64_t *b_full = fin + 1;                                // an instance's tap operands landed
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
-  volatile int32_t *s_shift = reinterpret_cast<volatile int32_t *>(misc + 136);  // [3] S of each stage's array
-  BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3]
+  BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3] per stage
   float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
+  BfRec *acc_rec = reinterpret_cast<BfRec *>(misc + 1536);   // [2] per accumulator
   float *xpose = reinterpret_cast<float *>(misc + kBfMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * blockIdx.x / gridDim.x);
@@ -107,7 +120,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *stop = 0;
   }
-  if (warp == 8) {
+  if (warp == kBfMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(256u)
                  : "memory");
@@ -123,7 +136,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     *stop = 1;
   };
 
-  if (warp == 9) {
+  if (warp == kBfProdWarp) {
     // ================================================================ producer
     int issued = 0;
     for (int i = 0; i < n; ++i) {
@@ -183,7 +196,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       for (int i = max(0, issued - kBfStages); i < issued; ++i)
         mbar_wait_bounded(smem_u32(&raw_full[i % kBfStages]), (i / kBfStages) & 1, bp.timeout_ns);
     __syncwarp();
-  } else if (warp == 8) {
+  } else if (warp == kBfMmaWarp) {
     // ================================================================ MMA
     if (lane == 0) {
       bool any = false;
@@ -198,7 +211,9 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           break;
         }
         tc_fence_after();
-        const int S = s_shift[st];
+        const BfRec r = rec[st];
+        acc_rec[i & 1] = r;  // read back once the GEMMs complete
+        const int S = r.S;
         const uint64_t dah = umma_desc_sw128(smem_u32(stage0 + st * kBfStageBytes));
         const uint64_t dlo = static_cast<uint64_t>((kTGroups + S) * 64);  // lo array after hi
         const uint64_t dbf = umma_desc_sw128(smem_u32(bops));
@@ -222,85 +237,28 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       }
     }
     __syncwarp();
-  } else {
-    // ================================================================ warps 0-7
+  } else if (warp < 8) {
+    // ================================================================ converter
     int loaded = -1;
-    // bounded wait by every thread of warps 0-7, outcome combined
-    auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
-      const bool w = mbar_wait_bounded(smem_u32(mb), par, bp.timeout_ns);
-      return bf_bar_and(w && !*stop);
-    };
-    // accumulator of item ip back: y = (hi part + lo part) / 2^8 to the FIR
-    // output frame, row energies, then the block energies in a fixed order
-    auto epilogue = [&](int ip, const BfRec &r) {
-      const int rows_valid = r.nv / kTR;
-      const int q4 = warp & 3, hf = warp >> 2;  // TMEM lane quarter, output half (16 complex)
-      const int m = q4 * 32 + lane;             // GEMM row: output chunk jc
-      const int jc = 16 * (m & 7) + (m >> 3);
-      const uint32_t ta = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>((ip & 1) * 128 + hf * 32);
-      float v[32], w[32];
-      tmem_ld32(ta, v);
-      tmem_ld32(ta + 64u, w);
-      tmem_ld_wait();
-      float e = 0.f;
-      const float sc = 1.f / kTScale;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        v[q] = (v[q] + w[q]) * sc;
-        e = fmaf(v[q], v[q], e);
-      }
-      eth[hf * 128 + jc] = jc < rows_valid ? e : 0.f;
-      // y through a per-warp transpose: a store instruction then writes 8
-      // rows x 64 contiguous bytes instead of 32 rows x 16 bytes.  Chunk f
-      // of row x sits at chunk f ^ ((x >> 1) & 3): conflict-free both ways.
-      float *wx = xpose + warp * 512;
-#pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-          *reinterpret_cast<float4 *>(wx + lane * 16 + ((f ^ ((lane >> 1) & 3)) << 2)) =
-              make_float4(v[16 * h2 + 4 * f], v[16 * h2 + 4 * f + 1], v[16 * h2 + 4 * f + 2], v[16 * h2 + 4 * f + 3]);
-        __syncwarp();
-#pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) {
-          const int x = 8 * e4 + (lane >> 2), fq = lane & 3;  // row of the warp, 16-byte chunk
-          const float4 val = *reinterpret_cast<const float4 *>(wx + x * 16 + ((fq ^ ((x >> 1) & 3)) << 2));
-          const int mx = q4 * 32 + x, jx = 16 * (mx & 7) + (mx >> 3);
-          if (jx < rows_valid)
-            *reinterpret_cast<float4 *>(r.y + r.s0 + kTR * jx + 16 * hf + 2 * (4 * h2 + fq)) = val;
-        }
-        __syncwarp();
-      }
-      tc_fence_before();
-      bf_bar();
-      if (tid == 0) mbar_arrive(smem_u32(&acc_empty[ip & 1]));
-      const int nb = r.nv / B;
-      if (tid < nb) {
-        float E = 0.f;
-        for (int k = 0; k < rpb; ++k) {
-          const int c = tid * rpb + k;
-          E += eth[c] + eth[128 + c];
-        }
-        r.energy[r.s0 / B + tid] = E;
-      }
-    };
-
-    bool ok = true;
-    BfRec prev{};
     uint32_t b_par = 0;
+    // bounded wait by every thread of the group, outcome combined
+    auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
+      const bool w = ws_wait(smem_u32(mb), par, bp.timeout_ns, stop);
+      return bar256_and<1>(w && !*stop);
+    };
+    bool ok = true;
     for (int i = 0; i < n; ++i) {
       const int st = i % kBfStages;
       ok = wait_all(&raw_full[st], (i / kBfStages) & 1);
       if (!ok) break;
       const BfRec r = rec[st];
       const int S = r.S, nv = r.nv;
-      bool prev_done = i == 0;  // the GEMMs of item i-1 have completed
       const bool reload = r.inst != loaded;
       if (reload) {  // this instance's tap operands by bulk copy, once no GEMM reads the old ones
-        if (!prev_done) {
-          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
+        if (i > 0) {  // item i-1's stage freed: every GEMM up to item i-1 has completed
+          const int sp = (i - 1) % kBfStages;
+          ok = wait_all(&st_free[sp], ((i - 1) / kBfStages) & 1);
           if (!ok) break;
-          prev_done = true;
         }
         if (tid == 0) {
           mbar_arrive_tx(smem_u32(b_full), static_cast<uint32_t>(S + 1) * 2 * kTOpBytes);
@@ -336,7 +294,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       if (r.hout && r.s0 + nv == r.L)
         for (int m = tid; m < r.T - 1; m += kBfWork)
           r.hout[m] = reinterpret_cast<const float2 *>(stg)[kBfRawHalo + nv - (r.T - 1) + m];
-      bf_bar();  // every raw sample of the stage has been read
+      bar256<1>();  // every raw sample of the stage has been read
       unsigned char *ahi = stg, *alo = stg + (kTGroups + S) * 1024;
 #pragma unroll
       for (int k = 0; k < kBfMaxPieces; ++k) {
@@ -353,36 +311,92 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           *reinterpret_cast<uint4 *>(alo + off) = l4;
         }
       }
-      if (tid == 0) s_shift[st] = S;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {  // the tap operands (copied while the tile was converted)
         ok = wait_all(b_full, b_par);
         b_par ^= 1u;
         if (!ok) break;
       } else {
-        bf_bar();
+        bar256<1>();
       }
       if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
-      if (i >= 1) {  // item i-1's accumulator, read back while item i's GEMMs run
-        if (!prev_done) {
-          ok = wait_all(&mma_done[(i - 1) & 1], ((i - 1) >> 1) & 1);
-          if (!ok) break;
-        }
-        epilogue(i - 1, prev);
-      }
-      prev = r;
-    }
-    if (ok && n > 0) {
-      ok = wait_all(&mma_done[(n - 1) & 1], ((n - 1) >> 1) & 1);
-      if (ok) epilogue(n - 1, prev);
     }
     if (!ok && tid == 0) fail(22, 0);
+  } else {
+    // ================================================================ read-back
+    const int et = tid - kBfWork, ew = warp - 8;   // 0..255, 0..7
+    const int q4 = warp & 3, hf = ew >> 2;          // TMEM lane quarter, output half (16 complex)
+    const int m = q4 * 32 + lane;                   // GEMM row: output chunk jc
+    const int jc = 16 * (m & 7) + (m >> 3);
+    float *wx = xpose + ew * 512;
+    auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
+      const bool w = ws_wait(smem_u32(mb), par, bp.timeout_ns, stop);
+      return bar256_and<2>(w && !*stop);
+    };
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+      ok = wait_all(&mma_done[i & 1], (i >> 1) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      // accumulator of item i: y = (hi part + lo part) / 2^8 to the FIR
+      // output frame, row energies, then the block energies in a fixed order
+      const BfRec r = acc_rec[i & 1];
+      const int rows_valid = r.nv / kTR;
+      const uint32_t ta = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>((i & 1) * 128 + hf * 32);
+      float v[32], w[32];
+      tmem_ld32(ta, v);
+      tmem_ld32(ta + 64u, w);
+      tmem_ld_wait();
+      float e = 0.f;
+      const float sc = 1.f / kTScale;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        v[q] = (v[q] + w[q]) * sc;
+        e = fmaf(v[q], v[q], e);
+      }
+      // the accumulator is free once every thread has its rows
+      tc_fence_before();
+      bar256<2>();
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty[i & 1]));
+      eth[hf * 128 + jc] = jc < rows_valid ? e : 0.f;
+      // y through a per-warp transpose: a store instruction then writes 8
+      // rows x 64 contiguous bytes instead of 32 rows x 16 bytes.  Chunk f
+      // of row x sits at chunk f ^ ((x >> 1) & 3): conflict-free both ways.
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+          *reinterpret_cast<float4 *>(wx + lane * 16 + ((f ^ ((lane >> 1) & 3)) << 2)) =
+              make_float4(v[16 * h2 + 4 * f], v[16 * h2 + 4 * f + 1], v[16 * h2 + 4 * f + 2], v[16 * h2 + 4 * f + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const int x = 8 * e4 + (lane >> 2), fq = lane & 3;  // row of the warp, 16-byte chunk
+          const float4 val = *reinterpret_cast<const float4 *>(wx + x * 16 + ((fq ^ ((x >> 1) & 3)) << 2));
+          const int mx = q4 * 32 + x, jx = 16 * (mx & 7) + (mx >> 3);
+          if (jx < rows_valid)
+            *reinterpret_cast<float4 *>(r.y + r.s0 + kTR * jx + 16 * hf + 2 * (4 * h2 + fq)) = val;
+        }
+        __syncwarp();
+      }
+      bar256<2>();  // every row energy is in eth
+      const int nb = r.nv / B;
+      if (et < nb) {
+        float E = 0.f;
+        for (int k = 0; k < rpb; ++k) {
+          const int c = et * rpb + k;
+          E += eth[c] + eth[128 + c];
+        }
+        r.energy[r.s0 / B + et] = E;
+      }
+    }
+    if (!ok && et == 0) fail(24, 0);
   }
 
   // ---- leave: every role is done (or stopped); free tensor memory
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == kBfMmaWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
   }
