@@ -14,8 +14,9 @@
 //                per sample); on a change of instance, its tap operands are
 //                copied in once the GEMMs of the item before have completed;
 //   warp 16      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
-//                and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of two
-//                128-column TMEM accumulators, hands the item's record on
+//                and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of four
+//                128-column TMEM accumulators (all 512 columns: the GEMM
+//                time per item varies with T, the read-back's does not), hands the item's record on
 //                with the accumulator, and frees the stage by a commit once
 //                the GEMMs have read it;
 //   warps 8-15   read-back: y = the two column halves added, scaled, written
@@ -42,6 +43,7 @@ constexpr int kBfMmaWarp = 16, kBfProdWarp = 17;
 constexpr int kBfMaxShifts = 5;                 // T <= 129
 constexpr int kBfRawHalo = 128;                 // samples staged before a tile (S <= 4)
 constexpr int kBfStages = 3;
+constexpr int kBfAccs = 4;                      // TMEM accumulators of 128 columns
 constexpr uint32_t kBfRawBytes = (kBfRawHalo + kTTile) * 8;                     // 33 KB: raw tile + halo
 constexpr uint32_t kBfAOpBytes = 2u * (kTGroups + kBfMaxShifts - 1) * 1024;      // 40 KB: chunk array (hi | lo)
 constexpr uint32_t kBfStageBytes = kBfAOpBytes > kBfRawBytes ? kBfAOpBytes : kBfRawBytes;
@@ -99,15 +101,15 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   uint64_t *raw_full = reinterpret_cast<uint64_t *>(misc);  // [3] raw tile landed (and its record)
   uint64_t *a_full = raw_full + kBfStages;                   // [3] chunk array written
   uint64_t *st_free = a_full + kBfStages;                    // [3] the GEMMs reading the stage completed
-  uint64_t *mma_done = st_free + kBfStages;                  // [2] GEMMs into accumulator a completed
-  uint64_t *acc_empty = mma_done + 2;                        // [2] accumulator a read back
-  uint64_t *fin = acc_empty + 2;                             // the issuer's last commit, at exit
+  uint64_t *mma_done = st_free + kBfStages;                  // [4] GEMMs into accumulator a completed
+  uint64_t *acc_empty = mma_done + kBfAccs;                  // [4] accumulator a read back
+  uint64_t *fin = acc_empty + kBfAccs;                       // the issuer's last commit, at exit
   uint64_t *b_full = fin + 1;                                // an instance's tap operands landed
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
-  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 168);
+  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 172);
   BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3] per stage
   float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
-  BfRec *acc_rec = reinterpret_cast<BfRec *>(misc + 1536);   // [2] per accumulator
+  BfRec *acc_rec = reinterpret_cast<BfRec *>(misc + 1536);   // [4] per accumulator
   float *xpose = reinterpret_cast<float *>(misc + kBfMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * blockIdx.x / gridDim.x);
@@ -116,13 +118,13 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   const int B = bp.B, rpb = B / kTR;
 
   if (tid == 0) {
-    for (int q = 0; q < 3 * kBfStages + 6; ++q) mbar_init(smem_u32(raw_full + q), 1);
+    for (int q = 0; q < 3 * kBfStages + 2 * kBfAccs + 2; ++q) mbar_init(smem_u32(raw_full + q), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *stop = 0;
   }
   if (warp == kBfMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(256u)
+                 "r"(512u)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -206,18 +208,18 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           fail(20, 0);
           break;
         }
-        if (i >= 2 && !ws_wait(smem_u32(&acc_empty[i & 1]), ((i >> 1) - 1) & 1, bp.timeout_ns, stop)) {
+        if (i >= kBfAccs && !ws_wait(smem_u32(&acc_empty[i % kBfAccs]), ((i / kBfAccs) - 1) & 1, bp.timeout_ns, stop)) {
           fail(21, 0);
           break;
         }
         tc_fence_after();
         const BfRec r = rec[st];
-        acc_rec[i & 1] = r;  // read back once the GEMMs complete
+        acc_rec[i % kBfAccs] = r;  // read back once the GEMMs complete
         const int S = r.S;
         const uint64_t dah = umma_desc_sw128(smem_u32(stage0 + st * kBfStageBytes));
         const uint64_t dlo = static_cast<uint64_t>((kTGroups + S) * 64);  // lo array after hi
         const uint64_t dbf = umma_desc_sw128(smem_u32(bops));
-        const uint32_t d = tmem + static_cast<uint32_t>((i & 1) * 128);
+        const uint32_t d = tmem + static_cast<uint32_t>((i % kBfAccs) * 128);
         for (int sh = 0; sh <= S; ++sh) {
           const uint64_t ds = dah + static_cast<uint64_t>((S - sh) * 64);  // row group -sh
           const uint64_t db = dbf + static_cast<uint64_t>(sh * (2 * kTOpBytes / 16));
@@ -227,7 +229,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
             umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN128, 1u);
           }
         }
-        umma_commit(smem_u32(&mma_done[i & 1]));
+        umma_commit(smem_u32(&mma_done[i % kBfAccs]));
         umma_commit(smem_u32(&st_free[st]));
         any = true;
       }
@@ -335,14 +337,15 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     };
     bool ok = true;
     for (int i = 0; i < n; ++i) {
-      ok = wait_all(&mma_done[i & 1], (i >> 1) & 1);
+      const int a = i % kBfAccs;
+      ok = wait_all(&mma_done[a], (i / kBfAccs) & 1);
       if (!ok) break;
       tc_fence_after();
       // accumulator of item i: y = (hi part + lo part) / 2^8 to the FIR
       // output frame, row energies, then the block energies in a fixed order
-      const BfRec r = acc_rec[i & 1];
+      const BfRec r = acc_rec[a];
       const int rows_valid = r.nv / kTR;
-      const uint32_t ta = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>((i & 1) * 128 + hf * 32);
+      const uint32_t ta = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(a * 128 + hf * 32);
       float v[32], w[32];
       tmem_ld32(ta, v);
       tmem_ld32(ta + 64u, w);
@@ -357,7 +360,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       // the accumulator is free once every thread has its rows
       tc_fence_before();
       bar256<2>();
-      if (et == 0) mbar_arrive(smem_u32(&acc_empty[i & 1]));
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty[a]));
       eth[hf * 128 + jc] = jc < rows_valid ? e : 0.f;
       // y through a per-warp transpose: a store instruction then writes 8
       // rows x 64 contiguous bytes instead of 32 rows x 16 bytes.  Chunk f
@@ -398,7 +401,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   __syncthreads();
   if (warp == kBfMmaWarp) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
   }
 }
 
