@@ -33,6 +33,8 @@ struct prune_batch {
   BatchInst *inst_d = nullptr;
   std::vector<BatchInst> inst_h;
   int2 *fir_map = nullptr;
+  int32_t *fir_cta = nullptr;  // tensor-core FIR: per-CTA item ranges of equal estimated cost
+  int32_t fir_ctas = 0;        // their count (0: equal counts)
   int32_t *hx_map = nullptr;
   int32_t *hx_pre = nullptr;   // N = 64: selected-tile prefix (written by DET/SEL each step)
   uint32_t *hx_ctr = nullptr;
@@ -80,10 +82,32 @@ std::vector<int2> fir_order(const prune_batch *b, int32_t order) {
   return m;
 }
 
+// The tensor-core FIR's per-CTA shares of the item order m (equal
+// estimated cost), uploaded over b->fir_cta.
+bool upload_fir_partition(prune_batch *b, const std::vector<int2> &m) {
+  b->fir_ctas = 0;
+  if (!b->fir_tc || b->fir_tiles == 0) return true;
+  const int G = std::min(b->sms, b->fir_tiles);
+  std::vector<int32_t> cta(static_cast<size_t>(G) + 1);
+  batch_fir_tc_partition(
+      m.data(), b->fir_tiles, b->B, G,
+      [&](int32_t i, int64_t *F, int *T) {
+        *F = b->F[i];
+        *T = static_cast<int>(b->T[i]);
+      },
+      cta.data());
+  if (cudaMemcpy(b->fir_cta, cta.data(), sizeof(int32_t) * cta.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  b->fir_ctas = G;
+  return true;
+}
+
 prune_status enqueue_step(prune_batch *b, const float2 *x, int parity) {
   BatchParams bp{};
   bp.inst = b->inst_d;
   bp.fir_map = b->fir_map;
+  bp.fir_cta = b->fir_ctas > 0 ? b->fir_cta : nullptr;
+  bp.fir_ctas = b->fir_ctas;
   bp.hx_map = b->hx_map;
   bp.x = x;
   bp.n = b->n;
@@ -222,7 +246,9 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
                      (s = balloc(b, &b->hx_pre, static_cast<size_t>(n) + 1)) || (s = balloc(b, &b->hx_ctr, 1))))
     return bail(s);
   uint16_t *fops = nullptr;
-  if (b->fir_tc && (s = balloc(b, &fops, static_cast<size_t>(fops_n)))) return bail(s);
+  if (b->fir_tc && ((s = balloc(b, &fops, static_cast<size_t>(fops_n))) ||
+                    (s = balloc(b, &b->fir_cta, static_cast<size_t>(b->sms) + 1))))
+    return bail(s);
   int64_t to = 0, ho = 0, bo = 0, fo = 0;
   bool ok = true;
   for (int32_t i = 0; i < n && ok; ++i) {
@@ -263,6 +289,7 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
        cudaMemcpyAsync(b->hx_map, hx_map.data(), sizeof(int32_t) * hx_map.size(), cudaMemcpyHostToDevice,
                        b->stream) == cudaSuccess;
   ok = ok && batch_enable_smem(b->tp_max, B, N, b->fir_tc);
+  ok = ok && cudaStreamSynchronize(b->stream) == cudaSuccess && upload_fir_partition(b, fir_map);
   if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) {
     b->err = std::string("batch upload failed: ") + cudaGetErrorString(cudaGetLastError());
     return bail(PRUNE_ECUDA);
@@ -360,7 +387,8 @@ prune_status prune_batch_set_tuning(prune_batch *b, const prune_batch_tuning *t)
   if (t->fir_order != b->tuning.fir_order) {
     const std::vector<int2> m = fir_order(b, t->fir_order);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
-        cudaMemcpy(b->fir_map, m.data(), sizeof(int2) * m.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(b->fir_map, m.data(), sizeof(int2) * m.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        !upload_fir_partition(b, m))
       s = bfail(b, PRUNE_ECUDA, "prune_batch_set_tuning: map upload failed");
   }
   if (s == PRUNE_OK) {

@@ -471,7 +471,8 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
 static inline cudaError_t batch_launch_step(const BatchParams &bp, int tp_max, int sms, cudaStream_t stream,
                                             int hx_grid = 0) {
   if (bp.fir_tc)  // one persistent CTA per SM over equal shares of the tiles
-    batch_fir_tc_kernel<<<std::max(1, std::min(sms, bp.fir_tiles)), kBfThreads, kBfSmemBytes, stream>>>(bp);
+    batch_fir_tc_kernel<<<bp.fir_cta ? bp.fir_ctas : std::max(1, std::min(sms, bp.fir_tiles)), kBfThreads,
+                          kBfSmemBytes, stream>>>(bp);
   else
     batch_fir_kernel<<<bp.fir_tiles, kFirThreads, fir_smem_bytes(tp_max), stream>>>(bp, tp_max);
   batch_detsel_kernel<<<bp.n, kDetThreads, 0, stream>>>(bp);

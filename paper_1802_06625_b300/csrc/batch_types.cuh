@@ -29,9 +29,11 @@ struct BatchInst {
 struct BatchParams {
   const BatchInst *inst;
   const int2 *fir_map;      // FIR CTA -> (instance, tile of the instance), in launch order
+  const int32_t *fir_cta;   // tensor-core FIR: CTA c fires items [fir_cta[c], fir_cta[c + 1]) of fir_map,
+                            // fir_ctas CTAs (nullptr: equal counts over min(SMs, fir_tiles) CTAs)
   const int32_t *hx_map;    // HX work item -> instance (an instance's items are consecutive)
   const float2 *x;          // step input, all instances back to back
-  int32_t n, B, N, TS, parity, fir_tiles, hx_items;
+  int32_t n, B, N, TS, parity, fir_tiles, hx_items, fir_ctas;
   int32_t hx_chunk;         // > 0: CTA c fires items [c * hx_chunk, (c + 1) * hx_chunk); 0: grid-stride
   int32_t fir_tc;           // 1: FIR on tensor cores (TS = 4096, every instance has fops)
   int32_t *hx_pre;          // N = 64: [n + 1] selected 128-row tiles before each instance (written by DET/SEL)
