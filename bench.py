@@ -344,7 +344,7 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args, dev):
+def run_batched(args, dev, compare_plain=True):
     """Batched (one launch sequence for all instances, replayed as a CUDA
     graph) against plain (one graph object per instance, fired one by one),
     same frames, wall clock over K steps with the device synchronized."""
@@ -379,6 +379,11 @@ def run_batched(args, dev):
             "selected_fraction": sel_samples / float(samples),
             "note": "whole step (three launches) against the HBM copy bandwidth"}
     bt.close()
+    out = {"workload": b.name, "instances": b.instances, "samples_per_step": samples,
+           "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
+           "roofline": roof, "tuning": tuned, "candidates_ms": [round(c["ms"], 4) for c in candidates]}
+    if not compare_plain:
+        return out
 
     graphs = [Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=1, out_frames=1, device=dev.index) for w in ws_]
     offs, o = [], 0
@@ -402,11 +407,8 @@ def run_batched(args, dev):
     t_plain = (time.perf_counter() - t0) / args.steps
     for g in graphs:
         g.close()
-    return {"workload": b.name, "instances": b.instances, "samples_per_step": samples,
-            "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
-            "plain_Msamples_s": samples / t_plain / 1e6, "plain_ms_per_step": 1e3 * t_plain,
-            "speedup": t_plain / t_batched, "roofline": roof,
-            "tuning": tuned, "candidates_ms": [round(c["ms"], 4) for c in candidates],
+    return {**out, "plain_Msamples_s": samples / t_plain / 1e6, "plain_ms_per_step": 1e3 * t_plain,
+            "speedup": t_plain / t_batched,
             "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
                       "graph with the autotuned launch shape, plain = one graph object per instance (push, run, "
                       "drop per step)"}
@@ -645,6 +647,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--no-dpd", action="store_true", help="skip the DPD stream measurement")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched step (no plain comparison): a small process for profiling it")
     ap.add_argument("--serve-streams", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")
@@ -654,6 +658,11 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     w = synth.PLAIN_LARGE if args.workload == "plain_large" else synth.PLAIN_SMALL
+    if args.batched_only and args.impl == "ours":
+        r = run_batched(args, torch.device("cuda:0"), compare_plain=False)
+        print(json.dumps({"metric": "batched step Msamples/s", "value": r["batched_Msamples_s"], "unit": UNIT,
+                          "batched": r}))
+        return
     if args.impl == "reference":
         run_reference(args, w)
     else:
