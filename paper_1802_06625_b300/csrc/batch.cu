@@ -89,11 +89,11 @@ bool upload_fir_partition(prune_batch *b, const std::vector<int2> &m) {
   if (!b->fir_tc || b->fir_tiles == 0) return true;
   const int G = std::min(b->sms, b->fir_tiles);
   std::vector<int32_t> cta(static_cast<size_t>(G) + 1);
-  batch_fir_tc_partition(
-      m.data(), b->fir_tiles, b->B, G,
-      [&](int32_t i, int64_t *F, int *T) {
-        *F = b->F[i];
-        *T = static_cast<int>(b->T[i]);
+  fir_cost_partition(
+      m.data(), b->fir_tiles, kTTile, G,
+      [&](int32_t i, int64_t *samples, int *shifts) {
+        *samples = b->F[i] * b->B;
+        *shifts = tc_shifts(static_cast<int>(b->T[i]));
       },
       cta.data());
   if (cudaMemcpy(b->fir_cta, cta.data(), sizeof(int32_t) * cta.size(), cudaMemcpyHostToDevice) != cudaSuccess)

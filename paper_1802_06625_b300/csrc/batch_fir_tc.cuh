@@ -32,9 +32,7 @@
 // The issuing thread commits once more to a barrier of its own and waits
 // before tensor memory is freed.
 #pragma once
-#include <algorithm>
-#include <vector>
-
+#include "batch_partition.hpp"
 #include "batch_types.cuh"
 #include "tc_common.cuh"
 
@@ -60,37 +58,6 @@ static_assert((kTGroups + kBfMaxShifts - 1) * 64 % kBfWork == 0, "converter piec
 
 __host__ inline bool batch_fir_tc_supported(int B, int T_max) {
   return B % kTR == 0 && B <= kTTile && kTTile % B == 0 && tc_shifts(T_max) <= kBfMaxShifts;
-}
-
-// Contiguous shares of the items with equal estimated cost, one per CTA:
-// CTA c fires items cta[c] .. cta[c + 1] - 1 (G + 1 entries).  The cost of an
-// item is a least-squares fit over the CTAs of clock probes of this kernel
-// on B300 (in thousands of cycles): 2.1 + 2.2 per 4096 samples + 0.14 per
-// shift beyond two, and 2.2 more where the instance changes (its tap
-// operands are reloaded once the GEMMs before have drained).  Equal counts
-// left the slowest CTA 8 % above the mean.  inst_FT(i, &F, &T) gives the
-// frame length in blocks and the taps of map entry instance i.
-template <typename InstFT>
-__host__ inline void batch_fir_tc_partition(const int2 *map, int32_t items, int B, int G, InstFT inst_FT,
-                                            int32_t *cta) {
-  std::vector<double> pre(static_cast<size_t>(items) + 1, 0.0);
-  for (int32_t k = 0; k < items; ++k) {
-    int64_t F = 0;
-    int T = 1;
-    inst_FT(map[k].x, &F, &T);
-    const int64_t nv = std::min<int64_t>(kTTile, F * B - static_cast<int64_t>(map[k].y) * kTTile);
-    double w = 2.1 + 2.2 * static_cast<double>(nv) / kTTile + 0.14 * std::max(0, tc_shifts(T) - 2);
-    if (k == 0 || map[k - 1].x != map[k].x) w += 2.2;
-    pre[k + 1] = pre[k] + w;
-  }
-  cta[0] = 0;
-  for (int g = 1; g < G; ++g) {
-    const double target = pre[items] * g / G;
-    int32_t j = static_cast<int32_t>(std::lower_bound(pre.begin(), pre.end(), target) - pre.begin());
-    if (j > 0 && target - pre[j - 1] < pre[j] - target) --j;  // the nearer boundary
-    cta[g] = std::max(cta[g - 1], std::min(j, items));
-  }
-  cta[G] = items;
 }
 
 // Barriers over one group of 8 warps (256 threads), named kId (the first
