@@ -133,11 +133,21 @@ __global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
     px[q] = i < nv ? xs[i] : make_float2(0.f, 0.f);
     rx[q] = sqrtf(px[q].x * px[q].x + px[q].y * px[q].y);
   }
+  // past the first tile the halo is the same input samples for every
+  // branch: thread tid < HW reads its sample once and carries psi like the
+  // tile's own (no global load between a branch's window and its barrier)
+  float2 hx = make_float2(0.f, 0.f);
+  float hr = 0.f;
+  if (tid < HW && tile > 0 && tid - HW >= -H) {
+    hx = __ldg(base + s0 + (tid - HW));
+    hr = sqrtf(hx.x * hx.x + hx.y * hx.y);
+  }
   int wb = 0;  // window buffer of the next active branch
   for (int k = 0; k < p.K; ++k) {
     if (k > 0) {
 #pragma unroll
       for (int q = 0; q < kDpdSPT; ++q) px[q] = make_float2(px[q].x * rx[q], px[q].y * rx[q]);
+      hx = make_float2(hx.x * hr, hx.y * hr);
     }
     if (!((m >> k) & 1u)) continue;  // the same branch set for the whole CTA
     float2 *win = wins[wb];
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
       float2 v = make_float2(0.f, 0.f);
       if (i >= -H) {
         if (tile > 0) {
-          v = dpd_psi(base[s0 + i], k + 1);
+          v = hx;
         } else {
           const int lp = p.last[static_cast<int64_t>(k) * p.P + pi];
           if (lp >= 0) v = dpd_psi(p.x[static_cast<int64_t>(lp) * p.period + p.period + i], k + 1);
