@@ -85,116 +85,97 @@ __global__ void dpd_hist_kernel(const float2 *x, int64_t period, int32_t K, int3
   }
 }
 
-// One CTA per (tile of 2048 outputs, period).  For each branch that fires in
-// the period the psi_k window (NT-1 halo samples + the tile) is built in
-// shared memory and the branch's FIR accumulates into the thread's 8
-// outputs; taps t >= T are zero, so NT >= T taps are computed.
+// One CTA per (tile of 2048 outputs, period).  The input window (NT-1 halo
+// samples + the tile) is staged in shared memory once; each thread then
+// reads its own window slots (its 8 outputs and the NT-1 samples before
+// them) into registers and carries psi_k there across the branches,
+// psi_{k+1} = psi_k |x|, so a branch needs no shared memory and no barrier.
+// Only the first tile's halo differs per branch (the tail of psi_k over the
+// last earlier period where branch k fired, or the incoming token): the
+// threads whose window reaches it (tid 0 and 1) read it per branch.  Taps
+// t >= T are zero, so NT >= T taps are computed.
 template <int NT>
-__global__ void __launch_bounds__(kDpdThreads, 3) dpd_kernel(DpdParams p) {
+__global__ void __launch_bounds__(kDpdThreads, NT <= 10 ? 3 : 2) dpd_kernel(DpdParams p) {
   constexpr int HW = NT - 1;                                   // halo slots of the window
   constexpr int kWin = (HW + kDpdTile) + ((HW + kDpdTile) >> 3) + 2;
-  __shared__ __align__(16) float2 wins[2][kWin];  // double buffered: one barrier per branch
-  // the input tile, read once into registers before the first branch; its
-  // space is the second window, first written after the first branch's
-  // barrier
-  float2 *xs = wins[1];
-  static_assert(kWin >= kDpdTile, "the input tile fits in a window buffer");
+  constexpr int R = kDpdSPT + HW;                              // a thread's window slots
+  __shared__ __align__(16) float2 xw[kWin];  // slot w: x at sample s0 - HW + w; at the end, the outputs
   __shared__ float2 hs[kDpdMaxK * NT];
   const int tid = threadIdx.x;
   const int pi = blockIdx.y, tile = blockIdx.x;
   const int64_t s0 = static_cast<int64_t>(tile) * kDpdTile;
   const int nv = static_cast<int>(min(static_cast<int64_t>(kDpdTile), p.period - s0));
   const float2 *base = p.x + static_cast<int64_t>(pi) * p.period;
+  const int H = p.T - 1;
   const float4 *src = reinterpret_cast<const float4 *>(base + s0);
   for (int q = tid; q < kDpdTile / 2; q += kDpdThreads) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (2 * q < nv) v = __ldg(src + q);
-    xs[2 * q] = make_float2(v.x, v.y);
-    xs[2 * q + 1] = make_float2(v.z, v.w);
+    xw[pad_idx(HW + 2 * q)] = make_float2(v.x, v.y);
+    xw[pad_idx(HW + 2 * q + 1)] = make_float2(v.z, v.w);
+  }
+  if (tid < HW) {  // halo past the first tile: the input before s0 where a tap reaches
+    const int i = tid - HW;
+    float2 v = make_float2(0.f, 0.f);
+    if (tile > 0 && i >= -H) v = __ldg(base + s0 + i);
+    xw[pad_idx(tid)] = v;
   }
   for (int q = tid; q < p.K * NT; q += kDpdThreads) {
     const int k = q / NT, t = q % NT;
     hs[q] = t < p.T ? p.taps[k * p.T + t] : make_float2(0.f, 0.f);
   }
   const uint32_t m = p.mask[pi];
-  const int H = p.T - 1;
+  const int ob = tid * kDpdSPT;
+  __syncthreads();
+  float2 px[R];
+  float rx[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    px[q] = xw[pad_idx(ob + q)];
+    rx[q] = sqrtf(px[q].x * px[q].x + px[q].y * px[q].y);
+  }
+  const bool first_halo = tile == 0 && ob < HW;  // the window reaches before the period's first sample
   float2 acc[kDpdSPT];
 #pragma unroll
   for (int j = 0; j < kDpdSPT; ++j) acc[j] = make_float2(0.f, 0.f);
-  const int ob = tid * kDpdSPT;
-  __syncthreads();
-  // the thread's window elements i = tid + 256 q: psi_k carried across the
-  // branches, psi_{k+1} = psi_k |x| (|x| once per element)
-  float2 px[kDpdSPT];
-  float rx[kDpdSPT];
-#pragma unroll
-  for (int q = 0; q < kDpdSPT; ++q) {
-    const int i = tid + q * kDpdThreads;
-    px[q] = i < nv ? xs[i] : make_float2(0.f, 0.f);
-    rx[q] = sqrtf(px[q].x * px[q].x + px[q].y * px[q].y);
-  }
-  // past the first tile the halo is the same input samples for every
-  // branch: thread tid < HW reads its sample once and carries psi like the
-  // tile's own (no global load between a branch's window and its barrier)
-  float2 hx = make_float2(0.f, 0.f);
-  float hr = 0.f;
-  if (tid < HW && tile > 0 && tid - HW >= -H) {
-    hx = __ldg(base + s0 + (tid - HW));
-    hr = sqrtf(hx.x * hx.x + hx.y * hx.y);
-  }
-  int wb = 0;  // window buffer of the next active branch
   for (int k = 0; k < p.K; ++k) {
     if (k > 0) {
 #pragma unroll
-      for (int q = 0; q < kDpdSPT; ++q) px[q] = make_float2(px[q].x * rx[q], px[q].y * rx[q]);
-      hx = make_float2(hx.x * hr, hx.y * hr);
+      for (int q = 0; q < R; ++q) px[q] = make_float2(px[q].x * rx[q], px[q].y * rx[q]);
     }
     if (!((m >> k) & 1u)) continue;  // the same branch set for the whole CTA
-    float2 *win = wins[wb];
-    wb ^= 1;
-    // halo: window slot w < HW holds psi_k at sample s0 - HW + w of the
-    // branch's stream (zero where no tap reaches)
-    if (tid < HW) {
-      const int i = tid - HW;  // sample offset from s0, in [-HW, 0)
-      float2 v = make_float2(0.f, 0.f);
-      if (i >= -H) {
-        if (tile > 0) {
-          v = hx;
-        } else {
-          const int lp = p.last[static_cast<int64_t>(k) * p.P + pi];
-          if (lp >= 0) v = dpd_psi(p.x[static_cast<int64_t>(lp) * p.period + p.period + i], k + 1);
-          else if (p.hist) v = p.hist[k * H + H + i];
+    if (first_halo) {  // these slots hold zeros (rx = 0): set them to the branch's token
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int i = ob + q - HW;  // sample offset from the period's start
+        if (i < 0) {
+          float2 v = make_float2(0.f, 0.f);
+          if (i >= -H) {
+            const int lp = p.last[static_cast<int64_t>(k) * p.P + pi];
+            if (lp >= 0) v = dpd_psi(p.x[static_cast<int64_t>(lp) * p.period + p.period + i], k + 1);
+            else if (p.hist) v = p.hist[k * H + H + i];
+          }
+          px[q] = v;
         }
       }
-      win[pad_idx(tid)] = v;
     }
-#pragma unroll
-    for (int q = 0; q < kDpdSPT; ++q) win[pad_idx(HW + tid + q * kDpdThreads)] = px[q];
-    __syncthreads();
-    float2 r[kDpdSPT + HW];  // window slots ob .. ob + 7 + HW
-#pragma unroll
-    for (int q = 0; q < kDpdSPT + HW; ++q) r[q] = win[pad_idx(ob + q)];
     const float2 *h = hs + k * NT;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const float2 ht = h[t];
 #pragma unroll
-      for (int j = 0; j < kDpdSPT; ++j) cmac(acc[j], ht, r[HW + j - t]);
+      for (int j = 0; j < kDpdSPT; ++j) cmac(acc[j], ht, px[HW + j - t]);
     }
-    // the next active branch writes the other buffer; the one after it
-    // writes this one only after the next branch's barrier, by which time
-    // every thread has read this one
   }
-  // coalesced store through shared memory (a buffer no thread still reads
+  // coalesced store through shared memory (the window is no longer read
   // once every thread has passed this barrier)
   __syncthreads();
-  float2 *win = wins[0];
 #pragma unroll
-  for (int j = 0; j < kDpdSPT; ++j) win[pad_idx(ob + j)] = acc[j];
+  for (int j = 0; j < kDpdSPT; ++j) xw[pad_idx(ob + j)] = acc[j];
   __syncthreads();
   float4 *out = reinterpret_cast<float4 *>(p.y + static_cast<int64_t>(pi) * p.period + s0);
   for (int q = tid; 2 * q < nv; q += kDpdThreads) {
-    const float2 a = win[pad_idx(2 * q)], b = win[pad_idx(2 * q + 1)];
+    const float2 a = xw[pad_idx(2 * q)], b = xw[pad_idx(2 * q + 1)];
     out[q] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
