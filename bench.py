@@ -649,6 +649,8 @@ def main():
     ap.add_argument("--no-dpd", action="store_true", help="skip the DPD stream measurement")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched step (no plain comparison): a small process for profiling it")
+    ap.add_argument("--dpd-only", action="store_true",
+                    help="only the DPD stream: a small process for profiling it")
     ap.add_argument("--serve-streams", type=int, default=256)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")
@@ -662,6 +664,10 @@ def main():
         r = run_batched(args, torch.device("cuda:0"), compare_plain=False)
         print(json.dumps({"metric": "batched step Msamples/s", "value": r["batched_Msamples_s"], "unit": UNIT,
                           "batched": r}))
+        return
+    if args.dpd_only and args.impl == "ours":
+        r = run_dpd(args, torch.device("cuda:0"))
+        print(json.dumps({"metric": "DPD Msamples/s", "value": r["Msamples_s"], "unit": UNIT, "dpd": r}))
         return
     if args.impl == "reference":
         run_reference(args, w)
