@@ -41,7 +41,7 @@ def _case(seed, P, period, K, T):
     return x, taps, hist, masks
 
 
-@pytest.mark.parametrize("K,T,period", [(10, 10, 4096), (3, 7, 2056), (16, 16, 16), (1, 1, 64)])
+@pytest.mark.parametrize("K,T,period", [(10, 10, 4096), (3, 7, 2056), (16, 16, 16), (1, 1, 64), (16, 16, 4104)])
 def test_dpd_matches_oracle(Dp, K, T, period):
     P = 7
     x, taps, hist, masks = _case(11 + K + T, P, period, K, T)
