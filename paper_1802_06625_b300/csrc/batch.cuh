@@ -327,6 +327,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
     // ================================================================ warps 0-7
     int loaded = -1;
     uint32_t b_par = 0;
+    bool reload_open = false;  // an R copy issued and not yet seen to land
     auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
       const bool w = mbar_wait_bounded(smem_u32(mb), par, bp.timeout_ns);
       return bf_bar_and(w && !*stop);
@@ -394,6 +395,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
           bulk_g2s(smem_u32(b_hi), src, kTcOpBytes, smem_u32(b_full));
           bulk_g2s(smem_u32(b_lo), src + kTcOpBytes / 2, kTcOpBytes, smem_u32(b_full));
         }
+        reload_open = true;
         loaded = r.inst;
       }
       // the rows as the split-FP16 A operand, written over the stage once
@@ -430,8 +432,9 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {
         ok = wait_all(b_full, b_par);
-        b_par ^= 1u;
         if (!ok) break;
+        b_par ^= 1u;
+        reload_open = false;
       } else {
         bf_bar();
       }
@@ -449,7 +452,12 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
       ok = wait_all(&mma_done[(cnt - 1) & 1], ((cnt - 1) >> 1) & 1);
       if (ok) epilogue(cnt - 1, prev);
     }
-    if (!ok && tid == 0) fail(27);
+    // an R reload whose copy was not seen to land (the warps left on a failed
+    // wait): no copy may still write shared memory when the CTA leaves
+    if (!ok && tid == 0) {
+      fail(27);
+      if (reload_open) mbar_wait_bounded(smem_u32(b_full), b_par, bp.timeout_ns);
+    }
   }
 
   // ---- leave: every role is done (or stopped); free tensor memory

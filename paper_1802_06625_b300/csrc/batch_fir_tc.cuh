@@ -246,6 +246,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     // ================================================================ converter
     int loaded = -1;
     uint32_t b_par = 0;
+    bool reload_open = false;  // a tap copy issued and not yet seen to land
     // bounded wait by every thread of the group, outcome combined
     auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
       const bool w = ws_wait(smem_u32(mb), par, bp.timeout_ns, stop);
@@ -271,6 +272,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
             bulk_g2s(smem_u32(bops + sh * 2 * kTOpBytes), r.fops + static_cast<size_t>(sh) * 2 * 64 * 64,
                      2 * kTOpBytes, smem_u32(b_full));
         }
+        reload_open = true;
         loaded = r.inst;
       }
       // the tile as the permuted split-FP16 chunk array (the fused loops'
@@ -319,14 +321,20 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {  // the tap operands (copied while the tile was converted)
         ok = wait_all(b_full, b_par);
-        b_par ^= 1u;
         if (!ok) break;
+        b_par ^= 1u;
+        reload_open = false;
       } else {
         bar256<1>();
       }
       if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
     }
-    if (!ok && tid == 0) fail(22, 0);
+    // a tap reload whose copy was not seen to land (the group left on a
+    // failed wait): no copy may still write shared memory when the CTA leaves
+    if (!ok && tid == 0) {
+      fail(22, 0);
+      if (reload_open) mbar_wait_bounded(smem_u32(b_full), b_par, bp.timeout_ns);
+    }
   } else {
     // ================================================================ read-back
     const int et = tid - kBfWork, ew = warp - 8;   // 0..255, 0..7

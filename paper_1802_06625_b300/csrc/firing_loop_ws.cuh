@@ -90,6 +90,12 @@ static __device__ __forceinline__ void ws_publish_frame(const LoopParams &p, int
   __threadfence();
 }
 
+// Bounded waits for the raw stages of the last two of `armed` items.
+static __device__ __noinline__ void ws_drain_raw(uint64_t *raw_full, uint32_t armed, uint64_t timeout_ns) {
+  for (uint32_t x = armed > 2u ? armed - 2u : 0u; x < armed; ++x)
+    mbar_wait_bounded(smem_u32(&raw_full[x & 1u]), (x >> 1) & 1u, timeout_ns);
+}
+
 static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(TcLoopParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const LoopParams &p = tp.lp;
@@ -152,7 +158,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     uint64_t f0_seen = 0;
     int sentinels = 0;
     bool claimed_out = false;  // one failing claim per CTA
-    for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
+    uint32_t i = 0;            // items armed so far (a failed wait leaves before arming item i)
+    for (; sentinels < kWsGroups; ++i) {
       const int s = i & 1;
       if (i >= 2 && !ws_wait(smem_u32(&raw_empty[s]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop)) {
         if (lane == 0) fail(kActFir, 10, 0);
@@ -224,6 +231,10 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
         for (int m = lane; m < f.T - 1; m += 32) f.hist_out[m] = cur[f.L - (f.T - 1) + m];
     }
+    // after a failed wait the converter may not take the last two items: no
+    // copy may still write a stage when the CTA leaves (on the normal path
+    // both were taken and the waits return at once)
+    if (lane == 0) ws_drain_raw(raw_full, i, p.timeout_ns);
   } else if (warp == 1) {
     // ================================================================ MMA
     const uint64_t dbfir = umma_desc_sw128(smem_u32(bfir));
