@@ -263,6 +263,10 @@ def run_ours(args, w):
     # kind 6 is the warp-specialised loop when T <= 65 (at most 3 tap shifts)
     # unless PRUNE_TC_KERNEL=pipes selects the tile-pipeline loop
     ws_loop = os.environ.get("PRUNE_TC_KERNEL", "") != "pipes" and 1 + (w.T - 1 + 31) // 32 <= 3
+
+    def kind_name(k):  # the kernel that ran for a timing kind
+        return "firing_loop_ws_kernel" if k == 6 and ws_loop else KIND_NAMES[k]
+
     peaks = measured_peaks()
     runs = args.steps * ((frames + C - 1) // C)
     roof = None
@@ -301,7 +305,7 @@ def run_ours(args, w):
         if traffic is None and kind in TRAFFIC_PER_FRAME and w.name == synth.PLAIN_LARGE.name:
             traffic = TRAFFIC_PER_FRAME[kind] * frames_per_launch
         roof["traffic"] = traffic
-        roof["kernel"] = "firing_loop_ws_kernel" if kind == 6 and ws_loop else KIND_NAMES[kind]
+        roof["kernel"] = kind_name(kind)
         roof["avg_launch_ms"] = kms / kn
         roof["share"] = kms / max(sum(t for t, _ in times.values()), 1e-12)
 
@@ -315,7 +319,7 @@ def run_ours(args, w):
                        "l2": "inputs larger than L2 (%.1f GiB per step), no flush" % (frames * L * 8 / 2**30),
                        "parallelism": f"instance-sharded x{ws}" if ws > 1 else "single instance"},
             "roofline": roof, "gpu_launches": launches,
-            "kernel_ms_per_step": {KIND_NAMES[k]: t / args.steps for k, (t, n) in times.items() if n},
+            "kernel_ms_per_step": {kind_name(k): t / args.steps for k, (t, n) in times.items() if n},
             "clocks": clk.summary()}
 
     # the batched form: one frame of each of 512 uneven instances per step
