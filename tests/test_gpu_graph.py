@@ -250,3 +250,41 @@ def test_pull_overlapping_later_pushes_and_runs(G, path):
     recs += g.pull(prev)
     g.close()
     check_against_oracle(w, x.numpy(), recs)
+
+
+def test_plain_large_shape_in_bench_runs_sampled(G):
+    """The plain-large graph (F = 4096, B = 1024, T = 64, N = 32: the
+    warp-specialised tensor-core loop) fired as the bench fires it: frames
+    pushed by reference in runs of C = 336.  Two runs (340 frames); sampled
+    frames on both sides of the run boundary against the oracle, each fed
+    the frame before it for its delay token."""
+    from paper_1802_06625_b300 import _lib
+
+    w = synth.PLAIN_LARGE
+    C, n = 336, 340
+    dev = torch.device("cuda", 0)
+    x = torch.empty(n, w.F, w.B, dtype=torch.complex64, device=dev)
+    for k in range(n):
+        x[k] = w.frame(k, device=dev)
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=C, out_frames=n, device=0)
+    for k in range(0, n, C):
+        m = min(C, n - k)
+        g.push(x[k:k + m], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+        assert g.run() == m
+    g.sync()
+    sample = [0, 1, 197, 335, 336, 339]
+    got, j = {}, 0
+    for s in sample:
+        if s > j:
+            assert g.discard(s - j) == s - j
+        (got[s],) = g.pull(1)
+        j = s + 1
+    g.close()
+    del x
+    for s in sample:
+        xs = torch.stack([w.frame(k) for k in range(max(0, s - 1), s + 1)]).numpy()
+        r = oracle.run(w.F, w.B, w.T, w.N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), xs)
+        frame, c, idx, y = got[s]
+        assert frame == s
+        err, rms, nb = compare_frame(c, idx, y, r.c[-1], r.idx[-1], r.y[-1], r.energy[-1], np.float32(w.tau), w.B)
+        assert rms > 0 and err <= TOL_REL * rms, (s, err / rms, nb)
