@@ -200,3 +200,73 @@ def test_delay_token_across_requests_and_periodic_input(S):
         if rms > 0:
             assert err <= TOL_REL * rms
     srv.close_server()
+
+
+def test_serving_workload_sampled_streams(S):
+    """The serving workload's 256 streams (B = 512, T = 32, N = 64, F up to
+    2048, 10 to 10^4 frames each, inputs read cyclically from the device
+    pool) through a server configured as the bench's (256 slots, 40 GB
+    budget, 16 frames per step, result rings of 32, two steps in flight),
+    admitted in arrival order as room frees up.  Every record is pulled;
+    the first, second and last frames of four streams are checked against
+    the oracle, each fed the frame before it for its delay token."""
+    sw = synth.SERVING
+    specs = [sw.stream(i) for i in range(sw.streams)]
+    fps = 16
+    pool = sw.pool_tensor(device="cuda")
+    srv = S.Server(sw.B, sw.N, F_max=sw.F_hi, T_max=sw.T, max_streams=256, hbm_budget=40 << 30,
+                   frames_per_step=fps, ring=2 * fps, max_inflight=2, device=0)
+    watch = [i for i in range(sw.streams) if specs[i]["frames"] <= 600][:4]
+    want = {i: {0, 1, specs[i]["frames"] - 1} for i in watch}
+    kept = {i: {} for i in watch}
+    pulled = [0] * sw.streams
+    nxt, sid_of = 0, {}
+    while nxt < sw.streams or sid_of:
+        while nxt < sw.streams:  # admission in arrival order
+            sp = specs[nxt]
+            sid = srv.open(sp["F"], sw.T, sp["tau"], sw.taps(nxt).numpy(), sw.H(nxt).numpy())
+            if sid is None:
+                break
+            L = sp["F"] * sw.B
+            srv.submit(sid, pool[sp["offset"]:sp["offset"] + sp["period"] * L], n=sp["frames"], period=sp["period"])
+            sid_of[sid] = nxt
+            nxt += 1
+        n = srv.step()
+        moved = 0
+        for sid, i in list(sid_of.items()):
+            while pulled[i] < specs[i]["frames"]:
+                k = pulled[i]
+                if i in want and k in want[i]:
+                    r = srv.pull(sid)
+                    if r is None:
+                        break
+                    kept[i][k] = r
+                elif srv.pull(sid, discard=True) is None:
+                    break
+                pulled[i] += 1
+                moved += 1
+            if pulled[i] == specs[i]["frames"]:
+                srv.close(sid)
+                del sid_of[sid]
+        if n == 0 and moved == 0:
+            srv.sync()
+    srv.sync()
+    srv.close_server()
+    poolh = pool.cpu()
+    for i in watch:
+        sp = specs[i]
+        L = sp["F"] * sw.B
+
+        def frame(k):  # the stream's frame k: pool frames read cyclically
+            o = sp["offset"] + (k % sp["period"]) * L
+            return poolh[o:o + L].reshape(sp["F"], sw.B)
+
+        for k in sorted(want[i]):
+            xs = torch.stack([frame(j) for j in range(max(0, k - 1), k + 1)]).numpy()
+            r = oracle.run(sp["F"], sw.B, sw.T, sw.N, np.float32(sp["tau"]), sw.taps(i).numpy(), sw.H(i).numpy(), xs)
+            fr, c, idx, y = kept[i][k]
+            assert fr == k
+            err, rms, nb = compare_frame(c, idx, y, r.c[-1], r.idx[-1], r.y[-1], r.energy[-1],
+                                         np.float32(sp["tau"]), sw.B)
+            if rms > 0:
+                assert err <= TOL_REL * rms, (i, k, err / rms, nb)
