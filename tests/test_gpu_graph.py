@@ -288,3 +288,42 @@ def test_plain_large_shape_in_bench_runs_sampled(G):
         assert frame == s
         err, rms, nb = compare_frame(c, idx, y, r.c[-1], r.idx[-1], r.y[-1], r.energy[-1], np.float32(w.tau), w.B)
         assert rms > 0 and err <= TOL_REL * rms, (s, err / rms, nb)
+
+
+def test_plain_large_host_frames_in_chunks_sampled(G):
+    """The end-to-end path at the plain-large shape: pinned host frames
+    pushed in chunks of 8 and fired, each chunk's records pulled to host
+    after the next chunk was pushed and fired (the bench's e2e pattern).
+    The records equal those of the same frames pushed by reference, and
+    sampled frames (both sides of a chunk boundary) match the oracle."""
+    from paper_1802_06625_b300 import _lib
+
+    w = synth.PLAIN_LARGE
+    E, ch = 24, 8
+    xh = torch.empty(E, w.F, w.B, dtype=torch.complex64).pin_memory()
+    for k in range(E):
+        xh[k] = w.frame(k, device="cuda").cpu()
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=336, out_frames=336, device=0)
+    recs = []
+    for k in range(0, E, ch):
+        g.push(xh[k:k + ch])
+        assert g.run() == ch
+        if k > 0:
+            recs += g.pull(ch)
+    recs += g.pull(ch)
+    g.close()
+    assert [r[0] for r in recs] == list(range(E))
+    xd = xh.cuda()
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=336, out_frames=336, device=0)
+    g.push(xd, mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+    assert g.run(sync=True) == E
+    ref = g.pull(E)
+    g.close()
+    for (fa, ca, ia, ya), (fb, cb, ib, yb) in zip(recs, ref):
+        assert fa == fb and ca == cb and np.array_equal(ia, ib) and np.array_equal(ya, yb), fa
+    for s in (0, 7, 8, 23):
+        xs = xh[max(0, s - 1):s + 1].numpy()
+        r = oracle.run(w.F, w.B, w.T, w.N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(), xs)
+        frame, c, idx, y = recs[s]
+        err, rms, nb = compare_frame(c, idx, y, r.c[-1], r.idx[-1], r.y[-1], r.energy[-1], np.float32(w.tau), w.B)
+        assert rms > 0 and err <= TOL_REL * rms, (s, err / rms, nb)
