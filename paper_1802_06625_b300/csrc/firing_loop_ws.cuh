@@ -65,8 +65,8 @@ struct WsGroup {
   long long prefix;
 };
 
-// Cold paths, kept out of line so the roles' loops stay compact in the
-// instruction caches.
+// Cold paths.  They stay inlined: as calls, the register saves around them
+// cost the hot loops more than their code does.
 // A wait ran out (or the CTA stops): the first reports it and the run aborts.
 static __device__ __forceinline__ void ws_fail(const LoopParams &p, volatile int32_t *stop, uint32_t actor,
                                             uint32_t where, uint64_t frame) {
