@@ -467,7 +467,7 @@ def run_serving(args, dev):
     fps = args.serve_fps
     srv = Server(sw.B, sw.N, F_max=sw.F_hi, T_max=sw.T, max_streams=args.serve_slots,
                  hbm_budget=int(args.serve_budget_gb * 2**30), frames_per_step=fps, ring=2 * fps,
-                 max_inflight=2, auto_release=True, device=dev.index)
+                 max_inflight=args.serve_inflight, auto_release=True, device=dev.index)
     # warm-up: one short stream end to end
     sid = srv.open(specs[0]["F"], sw.T, specs[0]["tau"], *params[0])
     srv.submit(sid, pool[:specs[0]["F"] * sw.B], n=2 * fps, period=1)
@@ -527,6 +527,7 @@ def run_serving(args, dev):
             "admission_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
             "steps": steps, "entries_per_step": entries / max(steps, 1), "peak_open_streams": peak_open,
             "frames_per_step": fps, "hbm_budget_GB": args.serve_budget_gb, "slots": args.serve_slots,
+            "steps_in_flight": args.serve_inflight,
             "timing": "host monotonic clock; arrival = scheduled Poisson time, completion = when the host saw "
                       "the stream's last step complete"}
 
@@ -668,6 +669,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-inflight", type=int, default=2, help="request-loop steps in flight")
     ap.add_argument("--traffic", type=float, default=None, help="ncu dram bytes per launch of the top kernel")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
