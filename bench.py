@@ -75,7 +75,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -115,6 +115,19 @@ class ClockSampler:
                 pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def host_description():
+    """The host the CPU baseline ran on: its logical CPUs and CPU model."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def dist_env():
@@ -183,7 +196,8 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 + Box-Muller)",
             "config": {"workload": w.name, "F": w.F, "B": w.B, "T": w.T, "N": w.N, "frames_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_description()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -331,6 +345,14 @@ def run_ours(args, w):
     if not args.no_dpd and ws == 1:
         line["dpd"] = run_dpd(args, dev)
 
+    # the 100-frame plain workload: throughput and per-frame latency
+    if not args.no_small and ws == 1:
+        line["plain_small"] = run_plain_small(args, dev)
+
+    # differentiation over the control trace: forward / backward, store vs recompute
+    if not args.no_diff and ws == 1:
+        line["differentiation"] = run_differentiation(args, dev)
+
     # the request loop: Poisson stream arrivals, admission by HBM budget
     if not args.no_serving and ws == 1:
         line["serving"] = run_serving(args, dev)
@@ -341,7 +363,8 @@ def run_ours(args, w):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, dt, nf = oracle_sample(w, args.cpu_frames, first=0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {nf} frame(s) of {w.name}, single-threaded FP64 C oracle, {dt:.1f} s"}
+                                "sample": f"first {nf} frame(s) of {w.name}, single-threaded FP64 C oracle, {dt:.1f} s",
+                                "host": host_description()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -371,23 +394,78 @@ def run_batched(args, dev, compare_plain=True):
         bt.fire(x, graph=True)
     bt.sync()
     t_batched = (time.perf_counter() - t0) / args.steps
-    # bytes the step must move: FIR 8 B in and 8 B out per sample, energies,
-    # idx, and HX 8 B in and 8 B out per selected sample
-    sel_samples = sum(bt.pull(i)[1] for i in range(b.instances)) * b.B
+    # algorithmic bytes of the step, as for the plain line: every input
+    # sample read once (8 B), every selected block written once with its
+    # index (8 B + 4 B per block); the bytes the three launches actually move
+    # (the FIR output written and read back between launches, energies) are
+    # reported beside them
+    sel_blocks = sum(bt.pull(i)[1] for i in range(b.instances))
+    sel_samples = sel_blocks * b.B
     blocks = sum(w.F for w in ws_)
-    step_bytes = 16.0 * samples + 16.0 * sel_samples + 8.0 * blocks
+    step_bytes = 8.0 * samples + (8.0 * b.B + 4.0) * sel_blocks
+    moved_bytes = 16.0 * samples + 16.0 * sel_samples + 8.0 * blocks + 4.0 * sel_blocks
     peaks = measured_peaks()
     roof = {"bound": "hbm", "achieved": step_bytes / t_batched / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "peak_source": "measured" if not peaks.get("fallback") else "fallback",
             "frac": step_bytes / t_batched / 1e9 / peaks["hbm_gbs"], "bytes_per_step": step_bytes,
+            "moved_bytes_per_step": moved_bytes, "moved_GBs": moved_bytes / t_batched / 1e9,
             "selected_fraction": sel_samples / float(samples),
-            "note": "whole step (three launches) against the HBM copy bandwidth"}
+            "note": "algorithmic bytes (8 B per input sample + (8B + 4) B per selected block) over the whole "
+                    "step's time, against the HBM copy bandwidth; moved_* counts the FIR output's round trip "
+                    "between the launches too"}
+    bt_off = list(bt.offsets)
     bt.close()
-    out = {"workload": b.name, "instances": b.instances, "samples_per_step": samples,
+    out = {"workload": b.name, "instances": b.instances, "samples_per_step": samples, "launches_per_step": 3,
            "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
            "roofline": roof, "tuning": tuned, "candidates_ms": [round(c["ms"], 4) for c in candidates]}
     if not compare_plain:
         return out
+
+    # plain with the same tensor-core kernels: one single-instance batch per
+    # instance, (a) fired one by one from the host (each its own CUDA-graph
+    # replay of its three launches), (b) all 512 x 3 launches captured in one
+    # CUDA graph, so that the batching gain is measured apart from the host
+    # launch cost
+    offs = []
+    for i in range(b.instances):
+        offs.append(bt_off[i])
+    cs = torch.cuda.Stream(device=dev)
+    singles = [Batch(b.B, b.N, [insts[i]], stream=cs, device=dev.index) for i in range(b.instances)]
+    xs = [x[offs[i]:offs[i] + ws_[i].F * ws_[i].B] for i in range(b.instances)]
+
+    def single_launches():
+        for sb, xi in zip(singles, xs):
+            sb.fire(xi, graph=True)
+
+    for _ in range(args.warmup):
+        single_launches()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        single_launches()
+    torch.cuda.synchronize(dev)
+    t_single = (time.perf_counter() - t0) / args.steps
+    for sb, xi in zip(singles, xs):       # one untimed pass outside the capture
+        sb.fire(xi, graph=False)
+    torch.cuda.synchronize(dev)
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=cs):
+        for sb, xi in zip(singles, xs):
+            sb.fire(xi, graph=False)
+    for _ in range(args.warmup):
+        cg.replay()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cg.replay()
+    torch.cuda.synchronize(dev)
+    t_one_graph = (time.perf_counter() - t0) / args.steps
+    del cg
+    for sb in singles:
+        sb.close()
+    out.update({"plain_tc_launches_ms_per_step": 1e3 * t_single, "plain_tc_one_graph_ms_per_step": 1e3 * t_one_graph,
+                "speedup_vs_plain_tc_launches": t_single / t_batched,
+                "speedup_vs_plain_tc_one_graph": t_one_graph / t_batched})
 
     graphs = [Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=1, out_frames=1, device=dev.index) for w in ws_]
     offs, o = [], 0
@@ -414,8 +492,9 @@ def run_batched(args, dev, compare_plain=True):
     return {**out, "plain_Msamples_s": samples / t_plain / 1e6, "plain_ms_per_step": 1e3 * t_plain,
             "speedup": t_plain / t_batched,
             "timing": "wall clock over K steps, device synchronized; batched = 3 launches replayed as one CUDA "
-                      "graph with the autotuned launch shape, plain = one graph object per instance (push, run, "
-                      "drop per step)"}
+                      "graph with the autotuned launch shape; plain = one graph object per instance (push, run, "
+                      "drop per step; the actor path, FIR on CUDA cores at N = 64); plain_tc = the same "
+                      "tensor-core kernels one instance per launch, fired from the host or captured as one graph"}
 
 
 def run_dpd(args, dev):
@@ -452,25 +531,41 @@ def run_dpd(args, dev):
             "paper": "PRUNE heterogeneous 106 Msamples/s on the RX platform (Table 4), other hardware: context only"}
 
 
-def run_serving(args, dev):
-    """Streams arrive on the host clock as a Poisson process; each is admitted
-    when a slot and room in the 40 GB budget are free, its frames queued as
-    one request, and every step fires the next frames of all admitted streams.
-    Latency of a stream = observed completion of its last frame - arrival."""
+def serve_once(args, dev, streams, lam, host_inputs=False):
+    """Streams arrive on the host clock as a Poisson process of rate lam;
+    each is admitted when a slot and room in the 40 GB budget are free, its
+    frames queued as one request, and every step fires the next frames of
+    all admitted streams.  Latency of a stream = observed completion of its
+    last frame - arrival.  host_inputs: a request's distinct frames (its
+    period of the pool) start in pinned host memory and are copied to the
+    device at admission, on the server's stream, inside the latency."""
     from paper_1802_06625_b300.serve import Server
 
-    sw = synth.ServingWorkload(**{**synth.SERVING.__dict__, "streams": args.serve_streams})
+    sw = synth.ServingWorkload(**{**synth.SERVING.__dict__, "streams": streams, "lam": lam})
     specs = [sw.stream(i) for i in range(sw.streams)]
     arr = sw.arrivals()
     params = [(sw.taps(i).numpy(), sw.H(i).numpy()) for i in range(sw.streams)]
     pool = sw.pool_tensor(device=dev)
+    pool_h = pool.cpu().pin_memory() if host_inputs else None
     fps = args.serve_fps
+    sstream = torch.cuda.Stream(device=dev)
     srv = Server(sw.B, sw.N, F_max=sw.F_hi, T_max=sw.T, max_streams=args.serve_slots,
                  hbm_budget=int(args.serve_budget_gb * 2**30), frames_per_step=fps, ring=2 * fps,
-                 max_inflight=args.serve_inflight, auto_release=True, device=dev.index)
+                 max_inflight=args.serve_inflight, auto_release=True, stream=sstream, device=dev.index)
+
+    def inputs(sp):
+        L = sp["F"] * sw.B
+        lo, hi = sp["offset"], sp["offset"] + sp["period"] * L
+        if not host_inputs:
+            return pool[lo:hi]
+        buf = torch.empty(hi - lo, dtype=torch.complex64, device=dev)
+        with torch.cuda.stream(sstream):
+            buf.copy_(pool_h[lo:hi], non_blocking=True)
+        return buf
+
     # warm-up: one short stream end to end
     sid = srv.open(specs[0]["F"], sw.T, specs[0]["tau"], *params[0])
-    srv.submit(sid, pool[:specs[0]["F"] * sw.B], n=2 * fps, period=1)
+    srv.submit(sid, inputs(specs[0])[:specs[0]["F"] * sw.B], n=2 * fps, period=1)
     while srv.step():
         pass
     srv.sync()
@@ -478,6 +573,7 @@ def run_serving(args, dev):
     srv.close(sid)
     srv.sync()
 
+    h2d = 0
     t0 = time.monotonic_ns()
     due = [t0 + int(a * 1e9) for a in arr]
     waiting, nxt, done_at, admitted_at, sid_of = [], 0, {}, {}, {}
@@ -496,8 +592,10 @@ def run_serving(args, dev):
             waiting.pop(0)
             sid_of[sid] = i
             admitted_at[i] = time.monotonic_ns()
-            L = sp["F"] * sw.B
-            srv.submit(sid, pool[sp["offset"]:sp["offset"] + sp["period"] * L], n=sp["frames"], period=sp["period"])
+            xin = inputs(sp)
+            if host_inputs:
+                h2d += xin.numel() * 8
+            srv.submit(sid, xin, n=sp["frames"], period=sp["period"])
         peak_open = max(peak_open, len(sid_of))
         n = srv.step()
         if n:
@@ -513,23 +611,155 @@ def run_serving(args, dev):
                 time.sleep(max(0.0, (due[nxt] - time.monotonic_ns()) * 1e-9))
     srv.sync()
     t1 = max(done_at.values())
-    st = srv.stats()
     srv.close_server()
     lat = np.array([(done_at[i] - due[i]) * 1e-6 for i in range(sw.streams)])
     wait = np.array([(admitted_at[i] - due[i]) * 1e-6 for i in range(sw.streams)])
     samples = sum(sp["frames"] * sp["F"] * sw.B for sp in specs)
-    return {"workload": sw.name, "streams": sw.streams, "lambda_per_s": sw.lam,
+    out = {"streams": sw.streams, "lambda_per_s": sw.lam, "samples": samples,
+           "offered_Msamples_s": samples / max(arr[-1], 1e-9) / 1e6,
+           "Msamples_s": samples / ((t1 - t0) * 1e-9) / 1e6, "makespan_s": (t1 - t0) * 1e-9,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+           "admission_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+           "steps": steps, "entries_per_step": entries / max(steps, 1), "peak_open_streams": peak_open}
+    if host_inputs:
+        out["h2d_bytes"] = h2d
+    return out
+
+
+def run_serving(args, dev):
+    """The request loop on the serving workload: the fixed trace of the
+    first second of arrivals at 2000 streams/s (offered load about twice what
+    one GPU sustains, so latencies include queueing), then a run at 0.7 of
+    the saturation rate measured on the trace, with inputs resident and with
+    inputs copied from host memory per request."""
+    trace = serve_once(args, dev, args.serve_streams, synth.SERVING.lam)
+    sw = synth.ServingWorkload(**{**synth.SERVING.__dict__, "streams": args.serve_streams_07})
+    mean_samples = np.mean([sp["frames"] * sp["F"] * sw.B for sp in (sw.stream(i) for i in range(sw.streams))])
+    lam_sat = trace["Msamples_s"] * 1e6 / mean_samples          # streams/s the GPU sustains
+    lam07 = 0.7 * lam_sat
+    r07 = serve_once(args, dev, args.serve_streams_07, lam07)
+    r07h = serve_once(args, dev, args.serve_streams_07, lam07, host_inputs=True)
+    return {"workload": synth.SERVING.name, "trace_streams": trace["streams"],
             "frames_per_stream": "log-uniform [10, 10^4]", "F": "uniform [64, 2048]",
-            "samples": samples, "Msamples_s": samples / ((t1 - t0) * 1e-9) / 1e6,
-            "makespan_s": (t1 - t0) * 1e-9,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "admission_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
-            "steps": steps, "entries_per_step": entries / max(steps, 1), "peak_open_streams": peak_open,
-            "frames_per_step": fps, "hbm_budget_GB": args.serve_budget_gb, "slots": args.serve_slots,
+            **trace, "lambda_saturation_per_s": lam_sat,
+            "lambda_0p7_sat": {**r07, "host_inputs": r07h},
+            "frames_per_step": args.serve_fps, "hbm_budget_GB": args.serve_budget_gb, "slots": args.serve_slots,
             "steps_in_flight": args.serve_inflight,
             "timing": "host monotonic clock; arrival = scheduled Poisson time, completion = when the host saw "
-                      "the stream's last step complete"}
+                      "the stream's last step complete; saturation rate = trace throughput / mean samples per "
+                      "stream of the 0.7 run's streams"}
+
+
+def run_plain_small(args, dev):
+    """The 100-frame plain workload (64 blocks x 256 samples, T = 16, H
+    16 x 16; the CUDA-core fused loop, N < 32): throughput over the whole
+    stream (frames resident on the device, pushed by reference, one launch,
+    CUDA events on the graph's stream), and the latency of one frame from
+    the host: pushed from pinned host memory, fired, its record pulled into
+    pinned host memory, one frame at a time (host clock, device synchronized
+    by the pull)."""
+    from paper_1802_06625_b300 import _lib
+    from paper_1802_06625_b300.graph import Graph
+
+    w = synth.PLAIN_SMALL
+    n = w.frames
+    x = torch.stack([w.frame(k, device=dev) for k in range(n)])
+    stream = torch.cuda.Stream(device=dev)
+    g = Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=n, out_frames=n, stream=stream, device=dev.index)
+
+    def step():
+        g.push(x, mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+        g.run()
+        g.discard()
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+    reps = max(args.steps, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    g.close()
+
+    # one frame at a time from the host
+    xh = x.cpu().pin_memory()
+    g = Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=3, out_frames=3, stream=stream, device=dev.index)
+    lib = _lib.lib()
+    ih = torch.empty(w.F, dtype=torch.int32).pin_memory()
+    yh = torch.empty(w.F, w.B, dtype=torch.complex64).pin_memory()
+    rec = (_lib.prune_frame_out * 1)()
+    rec[0].idx, rec[0].y = ih.data_ptr(), yh.data_ptr()
+    cnt = ctypes.c_int32()
+    lat = []
+    for rep in range(3):
+        for k in range(n):
+            t0 = time.perf_counter()
+            _lib.check(lib.prune_push_frames(g.h, xh[k].data_ptr(), 1, _lib.PRUNE_MEM_HOST), g.h)
+            g.run()
+            _lib.check(lib.prune_pull(g.h, rec, 1, ctypes.byref(cnt), _lib.PRUNE_MEM_HOST), g.h)
+            if rep > 0:
+                lat.append((time.perf_counter() - t0) * 1e3)
+    g.close()
+    lat = np.array(lat)
+    samples = n * w.F * w.B
+    return {"workload": w.name, "samples_per_step": samples, "Msamples_s": samples / (ms * 1e-3) / 1e6,
+            "ms_per_step": ms, "kernel": "firing_loop_kernel<16> (CUDA cores, N = 16)",
+            "frame_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                 "frames": int(lat.size)},
+            "note": "throughput: 100 device-resident frames per step in one launch (CUDA events, "
+                    f"{reps} steps); latency: host push (pinned) -> run -> host pull of one frame"}
+
+
+def run_differentiation(args, dev):
+    """Forward and backward of the differentiation workload (100 frames of
+    64 x 256 samples, T = 64, H 32 x 32, L2 loss against the sink output of
+    the graph with the seed-5 parameters) through torch.autograd over the
+    recorded control trace, with the FIR output stored or recomputed: CUDA
+    events per phase, peak device memory per mode."""
+    from paper_1802_06625_b300 import autodiff as AD
+
+    w = synth.DIFF
+    n = w.frames
+    x = torch.stack([w.frame(k, device=dev).reshape(-1) for k in range(n)])
+    taps0, H0 = w.taps().to(dev), w.H().to(dev)
+    tt, Ht = synth.taps(synth.DIFF_TARGET_SEED, w.T).to(dev), synth.hmat(synth.DIFF_TARGET_SEED, w.N).to(dev)
+    with torch.no_grad():
+        out_t, c_t, idx_t = AD.fire(tt, Ht, x, F=w.F, B=w.B, T=w.T, N=w.N, tau=w.tau)
+        target = AD.scatter(out_t, c_t, idx_t, w.F, w.B)
+    res = {}
+    for store in (True, False):
+        fwd, bwd = [], []
+        torch.cuda.synchronize(dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        for it in range(args.warmup + max(args.steps, 10)):
+            t = taps0.clone().requires_grad_(True)
+            h = H0.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            out, c, idx = AD.fire(t, h, x, F=w.F, B=w.B, T=w.T, N=w.N, tau=w.tau, store=store)
+            d = AD.scatter(out, c, idx, w.F, w.B) - target
+            loss = (d.real.square() + d.imag.square()).sum()
+            e1.record()
+            loss.backward()
+            e2.record()
+            torch.cuda.synchronize(dev)
+            if it >= args.warmup:
+                fwd.append(e0.elapsed_time(e1))
+                bwd.append(e1.elapsed_time(e2))
+        res["store" if store else "recompute"] = {
+            "forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
+            "peak_device_MB": (torch.cuda.max_memory_allocated(dev) - base) / 2**20}
+    samples = n * w.F * w.B
+    return {"workload": w.name, "samples_per_step": samples, **res,
+            "Msamples_s_fwd_bwd_store": samples / ((res["store"]["forward_ms"] + res["store"]["backward_ms"]) * 1e-3) / 1e6,
+            "note": "forward = FIR + DET/SEL + HX + scatter + loss; backward = HX and FIR adjoints (+ FIR "
+                    "recompute when not stored); medians over the timed iterations"}
 
 
 def copy_ceiling(xh, yh, d2h_bytes, dev, reps=3):
@@ -661,11 +891,16 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
     ap.add_argument("--no-dpd", action="store_true", help="skip the DPD stream measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 100-frame plain-small measurement")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched step (no plain comparison): a small process for profiling it")
     ap.add_argument("--dpd-only", action="store_true",
                     help="only the DPD stream: a small process for profiling it")
-    ap.add_argument("--serve-streams", type=int, default=256)
+    ap.add_argument("--serve-streams", type=int, default=2000,
+                    help="streams of the fixed trace (2000 = the first second of arrivals at 2000/s)")
+    ap.add_argument("--serve-streams-07", type=int, default=400,
+                    help="streams of the runs at 0.7 of the saturation rate")
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--serve-fps", type=int, default=16, help="frames a stream advances per step")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)

@@ -154,7 +154,14 @@ PRUNE_API prune_status prune_fifo_capacity(int64_t r, int64_t Q, int64_t C, int6
  * Sec. III-A), size the FIFOs by eq. (2), allocate the device state (FIFO
  * rings, device-side head/tail counters, delay token = T-1 zeros, taps, H) and
  * upload it.  *out receives the graph, or NULL on error (see
- * prune_last_error(NULL)).  ENOMEM if the allocation exceeds hbm_budget. */
+ * prune_last_error(NULL)).  ENOMEM if the allocation exceeds hbm_budget.
+ * Two buffers are allocated only when first needed, against the same
+ * budget: the staging ring of C frames for copied pushes (at the first push
+ * with PRUNE_MEM_HOST or PRUNE_MEM_DEVICE; borrowed pushes never need it),
+ * and the FIR output ring of C frames of the actor-per-kernel path (at
+ * creation when N >= 64, else at the first run with PRUNE_RUN_ACTORS; the
+ * fused loops keep the FIR output on chip).  A call that needs one beyond
+ * the budget returns ENOMEM and changes nothing. */
 PRUNE_API prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out);
 
 /* Free every device and host resource of the graph after waiting for its
@@ -470,6 +477,58 @@ PRUNE_API prune_status prune_model_buffer_bound(prune_model *m, int32_t fifo, in
 PRUNE_API prune_status prune_model_classify(prune_model *m, int32_t *form, int32_t *units);
 PRUNE_API const char *prune_model_last_error(const prune_model *m);
 
+/* What the model does not carry: the MoC fixes token rates, not what the
+ * actors compute, so the arithmetic of the runtime form's actors and the
+ * size of a token come with the compile call. */
+typedef struct prune_compile_params {
+  int32_t B;            /* samples per data token: a block (canonical) or a period (DPD) */
+  int32_t T;            /* taps of the FIR actor (of each FIR_k for DPD) */
+  int32_t N;            /* canonical: H is N x N (N divides B) */
+  int32_t C;            /* the buffering constant of eq. (2), >= 1 */
+  float tau;            /* canonical: DET threshold, v[b] = (E_b > tau) */
+  int32_t out_frames;   /* canonical: result records kept (0 = C) */
+  const float *taps;    /* host; canonical: 2*T floats; DPD: the caller keeps its taps */
+  const float *H;       /* host; canonical: 2*N*N floats, row-major */
+  void *stream;         /* canonical: passed to prune_graph_desc */
+  int32_t device;       /* canonical: passed to prune_graph_desc (-1 = current) */
+  int32_t reserved;
+  uint64_t hbm_budget;  /* canonical: passed to prune_graph_desc */
+} prune_compile_params;
+
+typedef struct prune_compiled {
+  int32_t form;              /* PRUNE_FORM_CANONICAL or PRUNE_FORM_DPD */
+  int32_t units;             /* DCs: F (canonical) or K (DPD) */
+  prune_graph_desc graph;    /* canonical: the descriptor for prune_graph_create (F = units) */
+  int32_t dpd_K, dpd_T;      /* DPD: K and T of prune_dpd_fire */
+  int64_t dpd_period;        /* DPD: samples per period (= B) */
+} prune_compiled;
+
+/* Compile a checked model into the runtime form that fires it (Sec. IV-V:
+ * the analysis must find no rate, type or design-rule violation and exactly
+ * one valid, consistent DPG; Sec. VI: the compiler maps the graph onto the
+ * runtime).  The canonical form is SRC -> FIR (a self-loop delay FIFO when
+ * T > 1) -> {DET, SEL}, DET's control to SEL and SINK, SEL -> HX_b -> SINK
+ * for the F DCs with control elements 1..F (element e = block e-1), token =
+ * one block, rates F on the FIR FIFOs, 1 elsewhere, no delays besides FIR's
+ * one token; it fills out->graph for prune_graph_create.  The DPD form is
+ * a source feeding POLY (x) one period and CONF (q) one configuration
+ * token, CONF's control to POLY and ADD (y), POLY -> FIR_k (self-loop delay
+ * 1) -> ADD for K DCs with elements 1..K (element k = bit k-1 of the
+ * period's mask), ADD -> at most one static sink, token = one period; it
+ * fills dpd_K, dpd_T, dpd_period for prune_dpd_fire.  Any other model is
+ * rejected with PRUNE_EINVAL and the rule, FIFO or actor that keeps it out
+ * in prune_model_last_error(m).
+ *   fifo_role[f]     (caller array of n_fifos, or NULL with n_fifos = 0): the
+ *                    runtime FIFO model FIFO f becomes: canonical 0..7 = f0 (SRC
+ *                    -> FIR), f1 (delay line), f2 (-> DET), f3 (-> SEL), f4, f5
+ *                    (control to SEL, SINK), f6 (SEL -> HX_b), f7 (HX_b -> SINK);
+ *                    DPD 0 input, 1 configuration input, 2 POLY -> FIR_k, 3 delay
+ *                    line, 4 FIR_k -> ADD, 5 control, 6 adder output
+ *   fifo_capacity[f] its capacity in tokens by eq. (2) with C
+ * Host only; the model is not changed. */
+PRUNE_API prune_status prune_model_compile(prune_model *m, const prune_compile_params *p, prune_compiled *out,
+                                           int32_t *fifo_role, int64_t *fifo_capacity, int32_t n_fifos);
+
 /* ------------------------------------------------------------------------
  * Dynamic Predistortion workload (Sec. VII-A2): a polynomial actor feeds K
  * parallel T-tap complex FIR filters (the DCs of a DPG), a configuration
@@ -540,9 +599,10 @@ PRUNE_API prune_status prune_fir_adjoint(const void *x, const void *hist, const 
 
 /* The fused firing loop (FIR, DET, SEL, HX_b, SINK; N < 64) over `frames`
  * consecutive frames of one instance, for callers that cannot call
- * cudaMalloc: code that enqueues work while a CUDA graph is being captured,
- * real-time host threads that must not block in the allocator, deployments
- * with a fixed device-memory budget.  It allocates nothing: inputs and
+ * cudaMalloc: real-time host threads that must not block in the device
+ * allocator, and deployments whose device memory is budgeted and committed up
+ * front, where an allocation at firing time may fail or is not permitted.
+ * It allocates nothing: inputs and
  * outputs are the caller's, and its only scratch is a fixed array compiled
  * into the library (every GPU that loads the library holds it, about 527 KB,
  * until the process exits).  Results equal those of the graph entry points.

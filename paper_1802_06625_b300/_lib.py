@@ -33,6 +33,7 @@ EXPORTS = ("prune_fifo_capacity", "prune_graph_create", "prune_graph_destroy", "
            "prune_model_create", "prune_model_destroy", "prune_model_add_actor", "prune_model_add_port",
            "prune_model_connect", "prune_model_set_control", "prune_model_check", "prune_model_dpg",
            "prune_model_dc", "prune_model_buffer_bound", "prune_model_classify", "prune_model_last_error",
+           "prune_model_compile",
            "prune_server_create", "prune_server_destroy", "prune_server_open", "prune_server_submit",
            "prune_server_step", "prune_server_progress", "prune_server_poll", "prune_server_pull",
            "prune_server_close", "prune_server_sync", "prune_server_stats", "prune_server_last_error")
@@ -62,6 +63,16 @@ class prune_batch_tuning(ctypes.Structure):
 class prune_model_report(ctypes.Structure):
     _fields_ = [("rate_errors", I32), ("type_errors", I32), ("rule_errors", I32 * 5), ("n_dpgs", I32),
                 ("consistent", I32), ("first_error", ctypes.c_char * 256)]
+
+
+class prune_compile_params(ctypes.Structure):
+    _fields_ = [("B", I32), ("T", I32), ("N", I32), ("C", I32), ("tau", ctypes.c_float), ("out_frames", I32),
+                ("taps", P), ("H", P), ("stream", P), ("device", I32), ("reserved", I32), ("hbm_budget", U64)]
+
+
+class prune_compiled(ctypes.Structure):
+    _fields_ = [("form", I32), ("units", I32), ("graph", prune_graph_desc), ("dpd_K", I32), ("dpd_T", I32),
+                ("dpd_period", I64)]
 
 
 class prune_server_desc(ctypes.Structure):
@@ -126,6 +137,8 @@ def load(path: str | None = None):
         "prune_model_dc": [P, I32, I32, ctypes.POINTER(I32), I32, ctypes.POINTER(I32), ctypes.POINTER(I32)],
         "prune_model_buffer_bound": [P, I32, ctypes.POINTER(I64)],
         "prune_model_classify": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "prune_model_compile": [P, ctypes.POINTER(prune_compile_params), ctypes.POINTER(prune_compiled),
+                                ctypes.POINTER(I32), ctypes.POINTER(I64), I32],
         "prune_batch_get_tuning": [P, ctypes.POINTER(prune_batch_tuning)],
         "prune_fir_adjoint": [P, P, P, I32, I32, I32, I32, P, P],
         "prune_server_create": [ctypes.POINTER(prune_server_desc), ctypes.POINTER(P)],

@@ -267,10 +267,13 @@ prune_status prune_batch_create(const prune_graph_desc *descs, int32_t n, prune_
                          b->stream) == cudaSuccess &&
          cudaMemcpyAsync(const_cast<float2 *>(in.H), d.H, sizeof(float2) * N * N, cudaMemcpyHostToDevice,
                          b->stream) == cudaSuccess;
-    if (ok && bops) ok = hx_tc_prepare_b(in.H, N, const_cast<uint16_t *>(in.bops), b->stream) == cudaSuccess;
-    if (ok && fops) {  // block-Toeplitz tap operands (split FP16, 2^8 scale)
+    const TcScale sc = tc_scale_of(d.taps, d.T, d.H, N);
+    in.s_taps = sc.s_taps;
+    in.s_h = sc.s_h;
+    if (ok && bops) ok = hx_tc_prepare_b(in.H, N, sc.s_h, nullptr, const_cast<uint16_t *>(in.bops), b->stream) == cudaSuccess;
+    if (ok && fops) {  // block-Toeplitz tap operands (split FP16, scaled by 2^s_taps)
       in.fops = fops + fo;
-      tc_prepare_fir_kernel<<<dim3(64, tc_shifts(d.T)), 64, 0, b->stream>>>(in.taps, d.T, fops + fo);
+      tc_prepare_fir_kernel<<<dim3(64, tc_shifts(d.T)), 64, 0, b->stream>>>(in.taps, d.T, sc.s_taps, fops + fo);
       ok = cudaGetLastError() == cudaSuccess;
       fo += static_cast<int64_t>(tc_fir_ops_elems(d.T));
     }

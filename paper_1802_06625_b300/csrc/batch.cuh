@@ -186,12 +186,13 @@ static __global__ void __launch_bounds__(kHxThreads) batch_hx_cuda_kernel(BatchP
 constexpr int kBhxThreads = 320;
 constexpr uint32_t kBhxStageBytes = 2 * kTcOpBytes;                      // 64 KB: 128 rows x 512 bytes
 constexpr uint32_t kBhxXposeBytes = 8 * 2048;                            // 2 KB per work warp
-constexpr uint32_t kBatchHxSmemBytes = 2 * kTcOpBytes + 2 * kBhxStageBytes + 1024 + kBhxXposeBytes + 1024;
-// B, stages, misc, transpose buffers, alignment
+constexpr uint32_t kBhxMiscBytes = 2048;
+constexpr uint32_t kBatchHxSmemBytes = 2 * kTcOpBytes + 2 * kBhxStageBytes + kBhxMiscBytes + kBhxXposeBytes + 1024;
+// B, stages, misc (barriers, records, row exponents), transpose buffers, alignment
 
 struct BhxRec {
   float2 *out;        // the tile's first output row
-  int32_t inst, nrows, pad0, pad1;
+  int32_t inst, nrows, s_h, pad;  // s_h: the instance's R exponent
 };
 
 static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(BatchParams bp) {
@@ -211,7 +212,9 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 128);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
   BhxRec *rec = reinterpret_cast<BhxRec *>(misc + 256);      // [2]
-  float *xpose = reinterpret_cast<float *>(misc + 1024);     // [8 warps][32 rows][16 floats]
+  int32_t *s_tile = reinterpret_cast<int32_t *>(misc + 1024); // [2] the tile's exponent per stage
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 1088); // [8] work warps' largest |x|
+  float *xpose = reinterpret_cast<float *>(misc + kBhxMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RB = bp.B / kTcNc;                                // rows per block
   // this CTA's selected tiles [r0, r0 + cnt) of the step
@@ -268,7 +271,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
       const int nblk = nrows / RB, j0 = tau * kTcM / RB;
       unsigned char *stg = stage0 + st * kBhxStageBytes;
       if (lane == 0) {
-        rec[st] = BhxRec{in.out + static_cast<int64_t>(tau) * kTcM * kTcNc, ib, nrows, 0, 0};
+        rec[st] = BhxRec{in.out + static_cast<int64_t>(tau) * kTcM * kTcNc, ib, nrows, in.s_h, 0};
         mbar_arrive_tx(smem_u32(&raw_full[st]), static_cast<uint32_t>(nblk) * bp.B * 8);
       }
       __syncwarp();
@@ -335,7 +338,6 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
     auto epilogue = [&](int ip, const BhxRec &r) {  // accumulator of tile ip to the compacted output
       const int a = ip & 1;
       const int qd = warp & 3, hf = warp >> 2;
-      const int m = qd * 32 + lane;
       float v[64];
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
@@ -348,16 +350,20 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
       // through a per-warp transpose, 64 bytes of each row per round: a
       // store instruction writes 8 rows x 64 contiguous bytes.  Chunk f of
       // row x sits at chunk f ^ ((x >> 1) & 3): conflict-free both ways.
-      (void)m;
       float *wx = xpose + warp * 512;
-      const float sc = 1.f / kTcBScale;
+      float f1, f2;  // the tile's outputs times 2^-(s_tile + s_h)
+      pow2_pair(-(s_tile[a] + r.s_h), f1, f2);
+      if (f2 != 1.f) {  // a scale beyond one float factor (uniform, rare)
+#pragma unroll
+        for (int e = 0; e < 64; ++e) v[e] *= f2;
+      }
 #pragma unroll
       for (int h4 = 0; h4 < 4; ++h4) {
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           const float *vv = v + 16 * h4 + 4 * f;
           *reinterpret_cast<float4 *>(wx + lane * 16 + ((f ^ ((lane >> 1) & 3)) << 2)) =
-              make_float4(vv[0] * sc, vv[1] * sc, vv[2] * sc, vv[3] * sc);
+              make_float4(vv[0] * f1, vv[1] * f1, vv[2] * f1, vv[3] * f1);
         }
         __syncwarp();
 #pragma unroll
@@ -399,7 +405,9 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
         loaded = r.inst;
       }
       // the rows as the split-FP16 A operand, written over the stage once
-      // every thread has read its rows
+      // every thread has read its rows; the tile scaled by the power of two
+      // its largest component needs (none inside [2^0, 2^15): HX maps each
+      // row on its own, so one scale per tile is exact to undo)
       unsigned char *stg = stage0 + st * kBhxStageBytes;
       constexpr int kPer = kTcM * (kTcK / 8) / kTcThreads;  // 8 pieces of 8 floats
       float4 u[kPer][2];
@@ -419,7 +427,30 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
           u[k][1] = u[k][0];
         }
       }
+      {
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if (lane == 0) cred[warp] = wm;
+      }
       bf_bar();
+      uint32_t tmx = cred[0];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) tmx = max(tmx, cred[w]);
+      const int sx = tc_shift_bits(tmx);
+      if (tid == 0) s_tile[st] = sx;
+      if (sx != 0) {  // uniform
+        const float sc = exp2i(sx);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          u[k][0].x *= sc; u[k][0].y *= sc; u[k][0].z *= sc; u[k][0].w *= sc;
+          u[k][1].x *= sc; u[k][1].y *= sc; u[k][1].z *= sc; u[k][1].w *= sc;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const int q = tid + k * kTcThreads;

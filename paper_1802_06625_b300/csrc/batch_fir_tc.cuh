@@ -9,17 +9,20 @@
 //                shared record, writes the delay token before an instance's
 //                first tile, and copies the raw tile and its halo into one of
 //                3 stages with bulk copies (up to 3 items ahead);
-//   warps 0-7    converter: the tile is read into registers and written back
-//                over the same stage as the split-FP16 chunk array (same size
-//                per sample); on a change of instance, its tap operands are
-//                copied in once the GEMMs of the item before have completed;
+//   warps 0-7    converter: the tile is read into registers, scaled by the
+//                power of two its largest component (halo included) needs
+//                (none inside [2^0, 2^15)), and written back over the same
+//                stage as the split-FP16 chunk array (same size per sample);
+//                on a change of instance, its tap operands are copied in once
+//                the GEMMs of the item before have completed;
 //   warp 16      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
 //                and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of four
 //                128-column TMEM accumulators (all 512 columns: the GEMM
 //                time per item varies with T, the read-back's does not), hands the item's record on
 //                with the accumulator, and frees the stage by a commit once
 //                the GEMMs have read it;
-//   warps 8-15   read-back: y = the two column halves added, scaled, written
+//   warps 8-15   read-back: y = the two column halves added, scaled back by
+//                2^-(tile exponent + tap exponent), written
 //                to the instance's FIR output frame through a per-warp
 //                shared-memory transpose (8 rows x 64 contiguous bytes per
 //                store instruction), and the block energies (fixed order).
@@ -88,6 +91,7 @@ struct BfRec {
   const uint16_t *fops; // its tap operands
   int64_t s0, L;        // tile start, frame length (samples)
   int32_t inst, nv, S, T;
+  int32_t s_taps, sx;   // the taps' exponent, the tile's (set by the converter)
 };
 
 static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(BatchParams bp) {
@@ -109,6 +113,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 168);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 172);
   BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3] per stage
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 448); // [8] converter warps' largest |x|
   float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
   BfRec *acc_rec = reinterpret_cast<BfRec *>(misc + 1536);   // [4] per accumulator
   float *xpose = reinterpret_cast<float *>(misc + kBfMiscBytes);  // [8 warps][32 rows][16 floats]
@@ -182,6 +187,8 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
         r.nv = nv;
         r.S = S;
         r.T = T;
+        r.s_taps = in.s_taps;
+        r.sx = 0;
         rec[st] = r;
       }
       __syncwarp();
@@ -301,7 +308,23 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       if (r.hout && r.s0 + nv == r.L)
         for (int m = tid; m < r.T - 1; m += kBfWork)
           r.hout[m] = reinterpret_cast<const float2 *>(stg)[kBfRawHalo + nv - (r.T - 1) + m];
-      bar256<1>();  // every raw sample of the stage has been read
+      // the tile's scale: its largest component (halo included)
+      {
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < kBfMaxPieces; ++k)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if (lane == 0) cred[warp] = wm;
+      }
+      bar256<1>();  // every raw sample of the stage has been read, every warp's largest |x| is in cred
+      uint32_t tm = cred[0];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) tm = max(tm, cred[w]);
+      const int sx = tc_pow2_shift(__uint_as_float(tm));
+      const float xsc = exp2i(sx);
       unsigned char *ahi = stg, *alo = stg + (kTGroups + S) * 1024;
 #pragma unroll
       for (int k = 0; k < kBfMaxPieces; ++k) {
@@ -309,6 +332,10 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
         if (q < npieces) {
           const int row = q >> 3, pc = q & 7;
           const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+          if (sx != 0) {  // uniform
+            u[k][0].x *= xsc; u[k][0].y *= xsc; u[k][0].z *= xsc; u[k][0].w *= xsc;
+            u[k][1].x *= xsc; u[k][1].y *= xsc; u[k][1].z *= xsc; u[k][1].w *= xsc;
+          }
           uint4 h4, l4;
           split_pair(u[k][0].x, u[k][0].y, h4.x, l4.x);
           split_pair(u[k][0].z, u[k][0].w, h4.y, l4.y);
@@ -318,6 +345,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           *reinterpret_cast<uint4 *>(alo + off) = l4;
         }
       }
+      if (tid == 0) rec[st].sx = sx;  // read by the MMA warp after a_full
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {  // the tap operands (copied while the tile was converted)
         ok = wait_all(b_full, b_par);
@@ -352,8 +380,9 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       ok = wait_all(&mma_done[a], (i / kBfAccs) & 1);
       if (!ok) break;
       tc_fence_after();
-      // accumulator of item i: y = (hi part + lo part) / 2^8 to the FIR
-      // output frame, row energies, then the block energies in a fixed order
+      // accumulator of item i: y = (hi part + lo part) 2^-(sx + s_taps) to
+      // the FIR output frame, row energies, then the block energies in a
+      // fixed order
       const BfRec r = acc_rec[a];
       const int rows_valid = r.nv / kTR;
       const uint32_t ta = tmem + (static_cast<uint32_t>(q4 * 32) << 16) + static_cast<uint32_t>(a * 128 + hf * 32);
@@ -362,10 +391,17 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       tmem_ld32(ta + 64u, w);
       tmem_ld_wait();
       float e = 0.f;
-      const float sc = 1.f / kTScale;
+      float f1, f2;
+      pow2_pair(-(r.sx + r.s_taps), f1, f2);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] += w[q];
+      if (f2 != 1.f) {  // a scale beyond one float factor (uniform, rare)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] *= f2;
+      }
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        v[q] = (v[q] + w[q]) * sc;
+        v[q] *= f1;
         e = fmaf(v[q], v[q], e);
       }
       // the accumulator is free once every thread has its rows

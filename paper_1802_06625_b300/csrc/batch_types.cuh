@@ -24,6 +24,7 @@ struct BatchInst {
   float2 *out;            // compacted HX output, F*B
   int32_t F, T, TP, fir_tile0, hx_tile0, pad;
   float tau;
+  int32_t s_taps, s_h;    // exponents of the scaled tensor-core operands (TcScale, host-computed)
 };
 
 struct BatchParams {

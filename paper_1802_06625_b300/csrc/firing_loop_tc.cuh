@@ -18,7 +18,10 @@
 //
 // Accuracy: operands split a = a_hi + a_lo into FP16 and three products
 // (hi hi, hi lo, lo hi) accumulated in FP32 in tensor memory, ~2^-22
-// relative; the tap and H operands are pre-scaled by 2^8.
+// relative.  Every operand is scaled by a power of two first (tc_scale.cuh):
+// the taps and H per graph, the input per tile (its largest component,
+// halo included, in [2^14, 2^15)), the FIR output by the per-graph 2^m of
+// the L1 bound; energies and outputs are scaled back exactly.
 //
 // HX_b (N = 32): a FIR output row is exactly one row of N samples of a
 // block, so the selected blocks' FIR rows (read from TMEM) are compacted into
@@ -56,9 +59,10 @@ __host__ __device__ inline size_t tc_loop_smem_bytes(int T) {
 struct TcLoopParams {
   int32_t window;        // frames fired round-robin (tc_ticket_tile)
   LoopParams lp;
-  const uint16_t *fir_ops;
-  const uint16_t *hx_ops;
+  const uint16_t *fir_ops;   // taps scaled by 2^s_taps
+  const uint16_t *hx_ops;    // H scaled by 2^s_h
   int32_t ns;
+  int32_t s_taps, m, s_h;    // TcScale of the graph
 };
 
 __device__ __forceinline__ uint4 split_pack8(const float *v, bool lo) {
@@ -121,9 +125,11 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   float *red4 = Et + 128;                                             // [4]
   int32_t *s_rule = reinterpret_cast<int32_t *>(misc + 36);           // firing rule of the claimed tile
   long long *s_prefix = reinterpret_cast<long long *>(misc + 40);
+  uint32_t *s_red = reinterpret_cast<uint32_t *>(misc + 1664);       // [2][4] warps' largest |x| per pass
   uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 32);
 
   const int tid = cta_tid % kTPipeThreads, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
+  int sx_pred = 0;  // scale exponent of this pipeline's previous tile
   // barrier of this pipeline's 128 threads (named barrier 1 + pipe)
   auto psync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + pipe) : "memory"); };
 
@@ -218,59 +224,84 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     const int rows_valid = nv / kTR;
 
     // ---- FIR A operand: stored row R = 8 (g + S) + b holds chunk j = 16 b + g.
-    // A thread's global loads are issued in batches before conversion.
+    // A thread's global loads are issued in batches before conversion.  The
+    // tile is scaled by the pipeline's previous tile's power of two; its
+    // largest component (halo included), gathered on the way, checks that
+    // scale after the barrier, and a tile it does not fit is converted again.
     const float2 *cur = f.src.frame(k);
     const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
-    for (int q0 = 0; q0 < npieces; q0 += kTMaxPieces * kTPipeThreads) {
-      float v[kTMaxPieces][8];
-#pragma unroll
-      for (int i = 0; i < kTMaxPieces; ++i) {
-        const int q = q0 + tid + kTPipeThreads * i;
-        if (q >= npieces) continue;
-        const int row = q >> 3, pc = q & 7;
-        const int j = 16 * (row & 7) + (row >> 3) - S;
-        const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
-        if (j >= 0) {
-          if (kTR * j + 4 * pc < nv) {
-            const float4 *src = reinterpret_cast<const float4 *>(cur + pos0);
-            const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
-            v[i][0] = u0.x; v[i][1] = u0.y; v[i][2] = u0.z; v[i][3] = u0.w;
-            v[i][4] = u1.x; v[i][5] = u1.y; v[i][6] = u1.z; v[i][7] = u1.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[i][e] = 0.f;
-          }
+    auto load_piece = [&](int q, float (&v)[8]) {
+      const int row = q >> 3, pc = q & 7;
+      const int j = 16 * (row & 7) + (row >> 3) - S;
+      const int64_t pos0 = s0 + static_cast<int64_t>(j) * kTR + 4 * pc;
+      if (j >= 0) {
+        if (kTR * j + 4 * pc < nv) {
+          const float4 *src = reinterpret_cast<const float4 *>(cur + pos0);
+          const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
+          v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+          v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int64_t pos = pos0 + e;
-            const int64_t d = s0 - pos;
-            float2 x = make_float2(0.f, 0.f);
-            if (d <= f.T - 1) {
-              if (pos >= 0) x = cur[pos];
-              else if (prev) x = prev[f.L + pos];
-              else if (f.hist) x = f.hist[f.T - 1 + pos];
-            }
-            v[i][2 * e] = x.x;
-            v[i][2 * e + 1] = x.y;
+          for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t pos = pos0 + e;
+          const int64_t d = s0 - pos;
+          float2 x = make_float2(0.f, 0.f);
+          if (d <= f.T - 1) {
+            if (pos >= 0) x = cur[pos];
+            else if (prev) x = prev[f.L + pos];
+            else if (f.hist) x = f.hist[f.T - 1 + pos];
           }
+          v[2 * e] = x.x;
+          v[2 * e + 1] = x.y;
         }
       }
-#pragma unroll
-      for (int i = 0; i < kTMaxPieces; ++i) {
-        const int q = q0 + tid + kTPipeThreads * i;
-        if (q >= npieces) continue;
-        const int row = q >> 3, pc = q & 7;
-        const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-        *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v[i], false);
-        *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v[i], true);
-      }
-    }
+    };
     if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
       for (int i = tid; i < f.T - 1; i += kTPipeThreads) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    psync();
+    int sx = sx_pred;
+    for (int pass = 0;; ++pass) {
+      const float xsc = exp2i(sx);
+      float mx = 0.f;
+      for (int q0 = 0; q0 < npieces; q0 += kTMaxPieces * kTPipeThreads) {
+        float v[kTMaxPieces][8];
+#pragma unroll
+        for (int i = 0; i < kTMaxPieces; ++i) {
+          const int q = q0 + tid + kTPipeThreads * i;
+          if (q < npieces) load_piece(q, v[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kTMaxPieces; ++i) {
+          const int q = q0 + tid + kTPipeThreads * i;
+          if (q >= npieces) continue;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            mx = fmaxf(mx, fabsf(v[i][e]));
+            if (sx != 0) v[i][e] *= xsc;
+          }
+          const int row = q >> 3, pc = q & 7;
+          const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v[i], false);
+          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v[i], true);
+        }
+      }
+      // the tile's largest component, exchanged through the barrier that
+      // ends the conversion (a buffer per pass); a tile the predicted scale
+      // does not fit is converted once more with its own (uniform)
+      uint32_t *cr = s_red + 4 * pass;
+      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      if (lane == 0) cr[warp] = wm;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      psync();
+      const uint32_t tm = max(max(cr[0], cr[1]), max(cr[2], cr[3]));
+      if (pass == 1 || tc_shift_fits(tm, sx)) break;
+      sx = tc_shift_bits(tm);
+    }
+    sx_pred = sx;
 
     // ---- FIR GEMM: ns shifts x 3 passes x 4 K-steps of 128 x 64 x 16
     if (tid == 0) {
@@ -313,7 +344,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
 #pragma unroll
         for (int i = 0; i < 16; ++i) e = fmaf(t16[i], t16[i], e);
       }
-      eth[jc] = jc < rows_valid ? e * (1.f / (kTScale * kTScale)) : 0.f;
+      eth[jc] = jc < rows_valid ? mul_pow2(e, -2 * (sx + tp.s_taps)) : 0.f;
     }
     psync();
     // block energies: eth is ordered by chunk; block b owns [rpb b, rpb (b+1));
@@ -353,8 +384,10 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     psync();
     const int cnt = *s_cnt;
     // selected rows become rows of the HX A operand (the FIR operand area is
-    // free): the FIR accumulators are read a second time, half a row at a time
+    // free): the FIR accumulators are read a second time, half a row at a
+    // time, and scaled by 2^m
     {
+      const float hsc = exp2i(tp.m);
       const int rk = jc < rows_valid ? s_rank[jc / rpb] : -1;
       const int hrow = rk * rpb + jc % rpb;
 #pragma unroll
@@ -364,10 +397,10 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           float t16[16];
           tmem_ld16(tmem + tlane + static_cast<uint32_t>(hf * 32), t16);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) y[i] = t16[i] * (1.f / kTScale);
+          for (int i = 0; i < 16; ++i) y[i] = t16[i] * hsc;
           tmem_ld16(tmem + tlane + static_cast<uint32_t>(hf * 32 + 16), t16);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) y[16 + i] = t16[i] * (1.f / kTScale);
+          for (int i = 0; i < 16; ++i) y[16 + i] = t16[i] * hsc;
           tmem_ld_wait();
         }
         if (rk >= 0) {
@@ -435,6 +468,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
       psync();
       if (*s_flag) { failed = true; break; }
       tc_fence_after();
+      float f1, f2;  // HX outputs are H y 2^(sx + s_taps + m + s_h)
+      pow2_pair(-(sx + tp.s_taps + tp.m + tp.s_h), f1, f2);
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float o[32];
@@ -451,8 +486,10 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
         if (m < cnt * rpb) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
           float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
                                                  (m % rpb) * kTR + hf * 16);
+          if (f2 != 1.f)  // a scale beyond one float factor (uniform, rare)
+            for (int i = 0; i < 32; ++i) o[i] *= f2;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) st_global_v8(dst + 8 * i, o + 8 * i, 1.f / kTScale);
+          for (int i = 0; i < 4; ++i) st_global_v8(dst + 8 * i, o + 8 * i, f1);
         }
       }
     }

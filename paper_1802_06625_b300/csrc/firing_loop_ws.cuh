@@ -9,7 +9,12 @@
 //                   asynchronous copies (cp.async.bulk, mbarrier tx counts);
 //   warp 1          MMA: the FIR GEMMs of a tile into one of 4 TMEM slots;
 //   warps 2-5       converter: raw FP32 -> split-FP16 chunk array (the
-//                   permuted K-major 128B-swizzle operand), 2-buffer ring;
+//                   permuted K-major 128B-swizzle operand), 2-buffer ring,
+//                   with the tile scaled by the power of two of the
+//                   converter's previous tile; the tile's largest component
+//                   (halo included), gathered from the same registers, checks
+//                   that scale after the converter's barrier, and the rare
+//                   tile it does not fit is converted again with its own;
 //   warps 6-17      three epilogue groups, tiles taken round-robin: block
 //                   energies, DET and SEL, the HX_b operand written back into
 //                   the slot's free TMEM columns (two FP16 per column), HX_b as
@@ -49,10 +54,11 @@ __host__ __device__ inline size_t ws_loop_smem_bytes(int T) {
          2 * kWsAOpBytes + kWsMiscBytes;
 }
 
-// Per-item record passed along the pipeline (t = ~0: sentinel).
+// Per-item record passed along the pipeline (t = ~0: sentinel); sx is the
+// tile's scale exponent (set by the converter).
 struct WsItem {
   unsigned long long t;
-  int32_t k, tile, nv, pad;
+  int32_t k, tile, nv, sx;
 };
 
 // Shared scratch of one epilogue group.
@@ -122,6 +128,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 512);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 520);
   WsGroup *grp = reinterpret_cast<WsGroup *>(misc + 1024);          // [3]
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 4096);       // [4] converter warps' largest |x|
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
   const unsigned long long kSentinel = ~0ull;
@@ -291,6 +298,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     // ================================================================ converter
     const int ct = tid - 64;  // 0..127
     int sentinels = 0;
+    int sx_pred = 0;          // scale exponent of this converter's previous tile
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
       const int s = i & 1, b = i & 1;
       if (!ws_wait(smem_u32(&raw_full[s]), (i >> 1) & 1u, p.timeout_ns, stop)) {
@@ -301,7 +309,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         if (ct == 0) fail(kActFir, 14, 0);
         break;
       }
-      const WsItem it = item_raw[s];
+      WsItem it = item_raw[s];
       if (it.t != kSentinel) {
         const unsigned char *raw = raw0 + s * kWsRawBytes;
         unsigned char *ahi = aop0 + b * kWsAOpBytes;
@@ -309,49 +317,79 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         const int npieces = (kTGroups + S) * 64;
         // kWsConvBatch pieces per thread at a time: all their loads are
         // issued before the first split, so the load latency is paid once
-        // per batch
-        for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
-          float4 u[kWsConvBatch][2];
+        // per batch.  The pieces are scaled by 2^sx (no multiply for 2^0),
+        // sx predicted from the converter's previous tile; the tile's
+        // largest component, gathered on the way, is exchanged through the
+        // barrier that ends the conversion, and a tile whose prediction does
+        // not fit is converted once more with its own sx (uniform).
+        int sx = sx_pred;
+        for (int pass = 0;; ++pass) {
+          const float xsc = exp2i(sx);
+          float mx = 0.f;
+          for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
+            float4 u[kWsConvBatch][2];
 #pragma unroll
-          for (int r = 0; r < kWsConvBatch; ++r) {
-            const int q = q0 + 128 * r;
-            const int row = q >> 3, pc = q & 7;
-            const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
-            if (q < npieces && kTR * j + 4 * pc < it.nv) {
-              // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read
-              // their halves in the other order, so each quarter-warp load
-              // covers all 32 banks once
-              const float4 *src =
-                  reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
-              const int sw = (pc >> 2) & 1;
-              const float4 a0 = src[sw], a1 = src[sw ^ 1];
-              u[r][0] = sw ? a1 : a0;
-              u[r][1] = sw ? a0 : a1;
-            } else {
-              u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-              u[r][1] = u[r][0];
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < kWsConvBatch; ++r) {
-            const int q = q0 + 128 * r;
-            if (q < npieces) {
+            for (int r = 0; r < kWsConvBatch; ++r) {
+              const int q = q0 + 128 * r;
               const int row = q >> 3, pc = q & 7;
-              const uint32_t off =
-                  static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-              uint4 h4, l4;
-              split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
-              split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
-              split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
-              split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
-              *reinterpret_cast<uint4 *>(ahi + off) = h4;
-              *reinterpret_cast<uint4 *>(alo + off) = l4;
+              const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
+              if (q < npieces && kTR * j + 4 * pc < it.nv) {
+                // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read
+                // their halves in the other order, so each quarter-warp load
+                // covers all 32 banks once
+                const float4 *src =
+                    reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
+                const int sw = (pc >> 2) & 1;
+                const float4 a0 = src[sw], a1 = src[sw ^ 1];
+                u[r][0] = sw ? a1 : a0;
+                u[r][1] = sw ? a0 : a1;
+              } else {
+                u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                u[r][1] = u[r][0];
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < kWsConvBatch; ++r) {
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[r][0].x), fabsf(u[r][0].y)), fmaxf(fabsf(u[r][0].z), fabsf(u[r][0].w))));
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[r][1].x), fabsf(u[r][1].y)), fmaxf(fabsf(u[r][1].z), fabsf(u[r][1].w))));
+              if (sx != 0) {
+                u[r][0].x *= xsc; u[r][0].y *= xsc; u[r][0].z *= xsc; u[r][0].w *= xsc;
+                u[r][1].x *= xsc; u[r][1].y *= xsc; u[r][1].z *= xsc; u[r][1].w *= xsc;
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < kWsConvBatch; ++r) {
+              const int q = q0 + 128 * r;
+              if (q < npieces) {
+                const int row = q >> 3, pc = q & 7;
+                const uint32_t off =
+                    static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+                uint4 h4, l4;
+                split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
+                split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
+                split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
+                split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
+                *reinterpret_cast<uint4 *>(ahi + off) = h4;
+                *reinterpret_cast<uint4 *>(alo + off) = l4;
+              }
             }
           }
+          // cred has a buffer per (item parity, pass): no thread rewrites one
+          // that another may still read
+          uint32_t *cr = cred + ((i & 1u) * 2u + static_cast<uint32_t>(pass)) * 4u;
+          const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+          if (lane == 0) cr[warp - 2] = wm;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          const uint32_t tm = max(max(cr[0], cr[1]), max(cr[2], cr[3]));
+          if (pass == 1 || tc_shift_fits(tm, sx)) break;
+          sx = tc_shift_bits(tm);
         }
+        it.sx = sx;
+        sx_pred = sx;
+      } else {
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 128;" ::: "memory");
       if (ct == 0) {
         item_a[b] = it;
         mbar_arrive(smem_u32(&a_full[b]));
@@ -389,11 +427,12 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
       const int rows_valid = nv / kTR;
       const uint32_t slot = tmem + static_cast<uint32_t>(j * 128);
-      // ---- FIR rows = columns 0-63 + columns 64-127; energies; each
-      //      16-column quarter split into the HX operand over the columns
-      //      64 + 16 qd .. + 15 it came from (hi in the first 8, lo in the
-      //      next 8, two FP16 per column)
+      // ---- FIR rows = columns 0-63 + columns 64-127 (y 2^(sx + s_taps));
+      //      energies; each 16-column quarter, times 2^m, split into the HX
+      //      operand over the columns 64 + 16 qd .. + 15 it came from (hi in
+      //      the first 8, lo in the next 8, two FP16 per column)
       {
+        const float hsc = exp2i(tp.m);
         float en = 0.f;
 #pragma unroll 1
         for (int qd = 0; qd < 4; ++qd) {
@@ -407,12 +446,12 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
             const float y0 = v[2 * q] + w[2 * q], y1 = v[2 * q + 1] + w[2 * q + 1];
             en = fmaf(y0, y0, en);
             en = fmaf(y1, y1, en);
-            split_pair(y0 * (1.f / kTScale), y1 * (1.f / kTScale), hi[q], lo[q]);
+            split_pair(y0 * hsc, y1 * hsc, hi[q], lo[q]);
           }
           tmem_st8(slot + tlane + static_cast<uint32_t>(64 + 16 * qd), hi);
           tmem_st8(slot + tlane + static_cast<uint32_t>(72 + 16 * qd), lo);
         }
-        G.eth[jc] = jc < rows_valid ? en * (1.f / (kTScale * kTScale)) : 0.f;
+        G.eth[jc] = jc < rows_valid ? mul_pow2(en, -2 * (it.sx + tp.s_taps)) : 0.f;
         tmem_st_wait();
       }
       tc_fence_before();
@@ -493,17 +532,22 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       tc_fence_after();
       if (cnt > 0) {
         const int rk = jc < rows_valid ? G.rank[jc / rpb] : -1;
+        float f1, f2;  // HX outputs are H y 2^(sx + s_taps + m + s_h)
+        pow2_pair(-(it.sx + tp.s_taps + tp.m + tp.s_h), f1, f2);
 #pragma unroll 1
         for (int hf = 0; hf < 2; ++hf) {
           float o[32];
           tmem_ld32(slot + tlane + static_cast<uint32_t>(hf * 32), o);
           tmem_ld_wait();
+          if (f2 != 1.f) {  // a scale beyond one float factor (uniform, rare)
+#pragma unroll
+            for (int q = 0; q < 32; ++q) o[q] *= f2;
+          }
           if (rk >= 0) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
             float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
                                                    hf * 16);
-            const float sc = 1.f / kTScale;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) st_global_v8(dst + 8 * q, o + 8 * q, sc);
+            for (int q = 0; q < 4; ++q) st_global_v8(dst + 8 * q, o + 8 * q, f1);
           }
         }
       }

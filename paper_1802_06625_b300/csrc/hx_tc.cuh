@@ -11,8 +11,11 @@
 // cores: every operand is split a = a_hi + a_lo (a_hi = fp16(a),
 // a_lo = fp16(a - a_hi)) and D = A_hi R_hi + A_hi R_lo + A_lo R_hi with FP32
 // accumulation in tensor memory (the dropped A_lo R_lo term is ~2^-22
-// relative).  R is pre-scaled by 2^8 so that R_lo stays in FP16's normal
-// range; the epilogue multiplies by 2^-8 (exact).
+// relative).  Both operands are scaled by powers of two before the split
+// (tc_scale.cuh): R once per graph by 2^s_h (its largest component in
+// [2^14, 2^15)), each row of A by its own 2^s_row (likewise: HX is applied
+// row by row, so a row's scale is exact to undo); the epilogue multiplies the
+// row's outputs by 2^-(s_row + s_h).
 //
 // Tile: M = 128 rows of selected blocks (gathered through the control
 // token's idx, read on the device), N = 128, K = 128; 3 x 8 MMAs of
@@ -24,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include "hx_cuda.cuh"
+#include "tc_scale.cuh"
 
 namespace prune {
 
@@ -32,9 +36,8 @@ constexpr int kTcNc = 64;               // complex N handled on tensor cores
 constexpr int kTcM = 128;               // rows per tile
 constexpr int kTcK = 2 * kTcNc;         // 128 real
 constexpr int kTcNg = 2 * kTcNc;        // 128 real outputs
-constexpr float kTcBScale = 256.f;
 constexpr uint32_t kTcOpBytes = kTcM * kTcK * 2;  // 32 KB per operand half
-constexpr uint32_t kTcSmemBytes = 4 * kTcOpBytes + 64 + 1024;
+constexpr uint32_t kTcSmemBytes = 4 * kTcOpBytes + 64 + 512 + 1024;  // operands, misc, row exponents, alignment
 
 __host__ __device__ inline bool hx_tc_supported(int N) { return N == kTcNc; }
 __host__ inline size_t hx_tc_b_elems(int N) { return 2 * static_cast<size_t>(2 * N) * (2 * N); }
@@ -47,15 +50,17 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows)
                                ((k & 7) << 1));
 }
 
-// R (scaled) split into hi / lo FP16 in the shared-memory layout.
-static __global__ void hx_tc_prepare_b_kernel(const float2 *H, uint16_t *bops) {
+// R scaled by 2^sh (TcScale::s_h; *sh_dev when that is not null), split
+// into hi / lo FP16 in the shared-memory layout.
+static __global__ void hx_tc_prepare_b_kernel(const float2 *H, int sh, const int32_t *sh_dev, uint16_t *bops) {
+  if (sh_dev) sh = *sh_dev;
   const int n = blockIdx.x, k = threadIdx.x;  // 128 x 128
   const int i = n >> 1, kk = k >> 1;
   const float2 h = H[i * kTcNc + kk];
   float v;
   if ((n & 1) == 0) v = (k & 1) == 0 ? h.x : -h.y;
   else v = (k & 1) == 0 ? h.y : h.x;
-  v *= kTcBScale;
+  v *= exp2i(sh);
   const __half hi = __float2half_rn(v);
   const __half lo = __float2half_rn(v - __half2float(hi));
   const uint32_t off = sw128_off(n, k, kTcNg) >> 1;
@@ -63,9 +68,10 @@ static __global__ void hx_tc_prepare_b_kernel(const float2 *H, uint16_t *bops) {
   bops[kTcNg * kTcK + off] = __half_as_ushort(lo);
 }
 
-__host__ inline cudaError_t hx_tc_prepare_b(const float2 *H, int N, uint16_t *bops, cudaStream_t s) {
+__host__ inline cudaError_t hx_tc_prepare_b(const float2 *H, int N, int sh, const int32_t *sh_dev, uint16_t *bops,
+                                            cudaStream_t s) {
   if (!hx_tc_supported(N)) return cudaErrorInvalidValue;
-  hx_tc_prepare_b_kernel<<<kTcNg, kTcK, 0, s>>>(H, bops);
+  hx_tc_prepare_b_kernel<<<kTcNg, kTcK, 0, s>>>(H, sh, sh_dev, bops);
   return cudaGetLastError();
 }
 
@@ -163,7 +169,9 @@ __device__ __forceinline__ uint4 split_pack(const float (&v)[8], bool lo) {
 
 struct HxTcParams {
   HxParams p;
-  const uint16_t *bops;   // R hi | R lo in the swizzled layout
+  const uint16_t *bops;   // R hi | R lo in the swizzled layout (R scaled by 2^s_h)
+  int32_t s_h;
+  const int32_t *s_h_dev; // when not null, s_h is read from the device here
   int32_t tiles_per_frame;
   uint64_t timeout_ns;
 };
@@ -178,9 +186,11 @@ static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams 
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 4 * kTcOpBytes);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 4 * kTcOpBytes + 8);
   int32_t *s_flag = reinterpret_cast<int32_t *>(base + 4 * kTcOpBytes + 16);
+  int32_t *s_row = reinterpret_cast<int32_t *>(base + 4 * kTcOpBytes + 64);  // [128] row exponents
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RB = p.B / kTcNc;  // rows per block
+  const int s_h = tp.s_h_dev ? *tp.s_h_dev : tp.s_h;
 
   // R operands: once per CTA
   {
@@ -218,7 +228,9 @@ static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams 
     const float2 *yk = p.y + p.yslot.slot(k) * p.y_stride;
     const int32_t *idxk = p.idx + rs * p.F;
 
-    // A: 128 gathered rows, split hi / lo, swizzled (16 chunks of 8 per row)
+    // A: 128 gathered rows, each scaled by its own power of two, split hi /
+    // lo, swizzled (16 chunks of 8 per row: the 16 lanes of a half-warp hold
+    // one row, whose largest component they reduce by shuffles)
     for (int q = tid; q < kTcM * (kTcK / 8); q += kTcThreads) {
       const int m = q >> 4, cc = q & 15;
       const int gr = tau * kTcM + m;
@@ -233,6 +245,16 @@ static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams 
           v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
         }
       }
+      float mx = 0.f;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(v[e]));
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int sr = tc_pow2_shift(mx);
+      const float sc = exp2i(sr);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] *= sc;
+      if (cc == 0) s_row[m] = sr;
       const uint32_t off = sw128_off(m, cc * 8, kTcM);
       *reinterpret_cast<uint4 *>(a_hi + off) = split_pack(v, false);
       *reinterpret_cast<uint4 *>(a_lo + off) = split_pack(v, true);
@@ -286,10 +308,12 @@ static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams 
         const int j = gr / RB, r = gr % RB;
         float4 *dst = reinterpret_cast<float4 *>(p.out + p.oslot.slot(k) * p.out_stride + static_cast<int64_t>(j) * p.B +
                                                  r * kTcNc + hf * 32);
-        const float s = 1.f / kTcBScale;
+        float f1, f2;
+        pow2_pair(-(s_row[m] + s_h), f1, f2);
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-          dst[e] = make_float4(v[4 * e] * s, v[4 * e + 1] * s, v[4 * e + 2] * s, v[4 * e + 3] * s);
+          dst[e] = make_float4(v[4 * e] * f1 * f2, v[4 * e + 1] * f1 * f2, v[4 * e + 2] * f1 * f2,
+                               v[4 * e + 3] * f1 * f2);
       }
     }
     tc_fence_before();
@@ -307,12 +331,14 @@ static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams 
   }
 }
 
-__host__ inline cudaError_t launch_hx_tc(const HxParams &p, const uint16_t *bops, int sms, cudaStream_t s,
-                                         uint64_t timeout_ns = 2000000000ull) {
+__host__ inline cudaError_t launch_hx_tc(const HxParams &p, const uint16_t *bops, int s_h, const int32_t *s_h_dev,
+                                         int sms, cudaStream_t s, uint64_t timeout_ns = 2000000000ull) {
   if (!hx_tc_supported(p.N)) return cudaErrorInvalidValue;
   HxTcParams tp{};
   tp.p = p;
   tp.bops = bops;
+  tp.s_h = s_h;
+  tp.s_h_dev = s_h_dev;
   const int64_t rows_max = static_cast<int64_t>(p.F) * (p.B / kTcNc);
   tp.tiles_per_frame = static_cast<int32_t>((rows_max + kTcM - 1) / kTcM);
   tp.timeout_ns = timeout_ns;

@@ -702,6 +702,231 @@ prune_status prune_model_classify(prune_model *m, int32_t *form, int32_t *units)
   return PRUNE_OK;
 }
 
+namespace {
+
+// FIFOs with an input (dst) port, or an output (src) port, on the actor.
+std::vector<int> fifos_in(const prune_model *m, int a) {
+  std::vector<int> v;
+  for (size_t i = 0; i < m->fifos.size(); ++i)
+    if (m->ports[m->fifos[i].dst].actor == a) v.push_back(static_cast<int>(i));
+  return v;
+}
+std::vector<int> fifos_out(const prune_model *m, int a) {
+  std::vector<int> v;
+  for (size_t i = 0; i < m->fifos.size(); ++i)
+    if (m->ports[m->fifos[i].src].actor == a) v.push_back(static_cast<int>(i));
+  return v;
+}
+int src_actor(const prune_model *m, int f) { return m->ports[m->fifos[f].src].actor; }
+int dst_actor(const prune_model *m, int f) { return m->ports[m->fifos[f].dst].actor; }
+bool is_self_loop(const prune_model *m, int f) { return src_actor(m, f) == dst_actor(m, f); }
+std::string fname(const prune_model *m, int f) {
+  return "FIFO " + std::to_string(f) + " (" + m->name[src_actor(m, f)] + " -> " + m->name[dst_actor(m, f)] + ")";
+}
+
+// A model FIFO's role in the runtime form and whether its rate and delay are
+// the ones the runtime implements.  Sets m->err and returns false otherwise.
+bool need(prune_model *m, int f, int64_t rate, int64_t delay, int role, std::vector<int> &roles,
+          const char *what) {
+  const MFifo &x = m->fifos[f];
+  if (x.rate != rate || x.delay != delay) {
+    m->err = "prune_model_compile: " + fname(m, f) + " (" + what + ") has rate " + std::to_string(x.rate) +
+             " and delay " + std::to_string(x.delay) + "; the runtime form needs rate " + std::to_string(rate) +
+             " and delay " + std::to_string(delay);
+    return false;
+  }
+  roles[f] = role;
+  return true;
+}
+
+bool fail_form(prune_model *m, const std::string &msg) {
+  m->err = "prune_model_compile: " + msg;
+  return false;
+}
+
+// The canonical form: SRC -f0-> FIR (self-loop f1) -f2-> q, -f3-> x;
+// q -f4-> x, -f5-> y (control); x -f6_b-> HX_b -f7_b-> y, F DCs with the
+// control elements 1..F.  Token unit: one block.
+bool compile_canonical(prune_model *m, const Dpg &d, int32_t T, std::vector<int> &roles) {
+  const int64_t F = static_cast<int64_t>(d.dcs.size());
+  // x and q: their one SRP input each comes from the same static actor (FIR),
+  // F blocks per firing
+  int fir = -1;
+  for (int a : {d.x, d.q}) {
+    int n = 0;
+    for (int f : fifos_in(m, a)) {
+      if (m->ports[m->fifos[f].dst].kind == PRUNE_PORT_CTRL_IN) continue;
+      ++n;
+      const int s = src_actor(m, f);
+      if (fir < 0) fir = s;
+      if (s != fir || m->kind[s] != PRUNE_ACTOR_STATIC)
+        return fail_form(m, "the data inputs of " + m->name[d.q] + " and " + m->name[d.x] +
+                                " must both come from one static actor (FIR)");
+      if (!need(m, f, F, 0, a == d.q ? 2 : 3, roles, "FIR output")) return false;
+    }
+    if (n != 1) return fail_form(m, m->name[a] + " must have exactly one data input (from FIR)");
+  }
+  // control FIFOs: one to x, one to y, rate 1, no initial tokens
+  for (int f : fifos_out(m, d.q)) {
+    const int a = dst_actor(m, f);
+    if (a != d.x && a != d.y) return fail_form(m, m->name[d.q] + " may only feed the control ports of x and y");
+    if (!need(m, f, 1, 0, a == d.x ? 4 : 5, roles, "control")) return false;
+  }
+  // FIR: input f0 from a static source, the self-loop f1 (T > 1), outputs
+  // only to q and x
+  int src = -1, loops = 0;
+  for (int f : fifos_in(m, fir)) {
+    if (is_self_loop(m, f)) {
+      ++loops;
+      if (!need(m, f, 1, 1, 1, roles, "FIR delay line")) return false;
+      continue;
+    }
+    if (src >= 0) return fail_form(m, m->name[fir] + " must have one data input (from the source)");
+    src = src_actor(m, f);
+    if (!need(m, f, F, 0, 0, roles, "source")) return false;
+  }
+  if (src < 0 || m->kind[src] != PRUNE_ACTOR_STATIC || !fifos_in(m, src).empty())
+    return fail_form(m, "FIR's input must come from a static source actor without inputs");
+  if (loops > 1) return fail_form(m, m->name[fir] + " has more than one self-loop");
+  if (loops == 0 && T > 1)
+    return fail_form(m, m->name[fir] + " has no self-loop delay FIFO, so it carries no delay token; only T = 1 fits");
+  for (int f : fifos_out(m, fir))
+    if (!is_self_loop(m, f) && dst_actor(m, f) != d.q && dst_actor(m, f) != d.x)
+      return fail_form(m, m->name[fir] + " may only feed q, x and its own delay line");
+  for (int f : fifos_out(m, src))
+    if (dst_actor(m, f) != fir) return fail_form(m, "the source may only feed FIR");
+  if (!fifos_out(m, d.y).empty())
+    return fail_form(m, m->name[d.y] + " (SINK) must not feed other actors: its records go to the host");
+  // the DCs: one block in from x, one block out to y; elements 1..F
+  std::vector<char> seen(static_cast<size_t>(F) + 1, 0);
+  for (size_t k = 0; k < d.dcs.size(); ++k) {
+    const int a = d.dcs[k][0], e = d.dc_elem[k];
+    if (e < 1 || e > F || seen[e]) return fail_form(m, "DC " + m->name[a] + " has no unique control element in 1..F");
+    seen[e] = 1;
+    for (int f : fifos_in(m, a))
+      if (!need(m, f, 1, 0, 6, roles, "SEL -> HX_b")) return false;
+    for (int f : fifos_out(m, a))
+      if (!need(m, f, 1, 0, 7, roles, "HX_b -> SINK")) return false;
+  }
+  for (size_t f = 0; f < roles.size(); ++f)
+    if (roles[f] < 0) return fail_form(m, fname(m, static_cast<int>(f)) + " has no place in the canonical form");
+  return true;
+}
+
+// The DPD form: a static source feeds x (POLY) one period and q (CONF) one
+// configuration token; q's control goes to x and y (ADD); x -> FIR_k (self
+// loop) -> y for the K DCs with elements 1..K; y feeds at most one static
+// sink.  Token unit: one period.
+bool compile_dpd(prune_model *m, const Dpg &d, std::vector<int> &roles) {
+  const int64_t K = static_cast<int64_t>(d.dcs.size());
+  for (int a : {d.x, d.q}) {
+    int n = 0;
+    for (int f : fifos_in(m, a)) {
+      if (m->ports[m->fifos[f].dst].kind == PRUNE_PORT_CTRL_IN) continue;
+      ++n;
+      const int s = src_actor(m, f);
+      if (m->kind[s] != PRUNE_ACTOR_STATIC || !fifos_in(m, s).empty())
+        return fail_form(m, m->name[a] + "'s input must come from a static source actor without inputs");
+      if (!need(m, f, 1, 0, a == d.x ? 0 : 1, roles, a == d.x ? "input" : "configuration input")) return false;
+    }
+    if (n != 1) return fail_form(m, m->name[a] + " must have exactly one data input");
+  }
+  for (int f : fifos_out(m, d.q)) {
+    const int a = dst_actor(m, f);
+    if (a != d.x && a != d.y) return fail_form(m, m->name[d.q] + " may only feed the control ports of x and y");
+    if (!need(m, f, 1, 0, 5, roles, "control")) return false;
+  }
+  std::vector<char> seen(static_cast<size_t>(K) + 1, 0);
+  for (size_t k = 0; k < d.dcs.size(); ++k) {
+    const int a = d.dcs[k][0], e = d.dc_elem[k];
+    if (e < 1 || e > K || seen[e]) return fail_form(m, "DC " + m->name[a] + " has no unique control element in 1..K");
+    seen[e] = 1;
+    for (int f : fifos_in(m, a))
+      if (!need(m, f, 1, is_self_loop(m, f) ? 1 : 0, is_self_loop(m, f) ? 3 : 2, roles,
+                is_self_loop(m, f) ? "FIR_k delay line" : "POLY -> FIR_k"))
+        return false;
+    for (int f : fifos_out(m, a))
+      if (!is_self_loop(m, f) && !need(m, f, 1, 0, 4, roles, "FIR_k -> ADD")) return false;
+  }
+  for (int f : fifos_out(m, d.y)) {
+    const int s = dst_actor(m, f);
+    if (m->kind[s] != PRUNE_ACTOR_STATIC || !fifos_out(m, s).empty())
+      return fail_form(m, m->name[d.y] + " may only feed one static sink without outputs");
+    if (!need(m, f, 1, 0, 6, roles, "adder output")) return false;
+  }
+  for (size_t f = 0; f < roles.size(); ++f)
+    if (roles[f] < 0) return fail_form(m, fname(m, static_cast<int>(f)) + " has no place in the DPD form");
+  return true;
+}
+
+}  // namespace
+
+prune_status prune_model_compile(prune_model *m, const prune_compile_params *p, prune_compiled *out,
+                                 int32_t *fifo_role, int64_t *fifo_capacity, int32_t n_fifos) {
+  if (!m || !p || !out) return mfail(m, PRUNE_EINVAL, "prune_model_compile: NULL argument");
+  if (n_fifos < 0 || (n_fifos > 0 && (!fifo_role || !fifo_capacity)))
+    return mfail(m, PRUNE_EINVAL, "prune_model_compile: bad fifo_role / fifo_capacity arrays");
+  if (!m->done) analyse(m);
+  std::memset(out, 0, sizeof *out);
+  const prune_model_report &r = m->rep;
+  const std::string why = r.first_error[0] ? std::string(": ") + r.first_error : std::string();
+  if (r.rate_errors) return mfail(m, PRUNE_EINVAL, "prune_model_compile: FIFO rates do not match their ports (Sec. III-A)" + why);
+  if (r.type_errors) return mfail(m, PRUNE_EINVAL, "prune_model_compile: ports an actor type does not allow (Sec. III-B)" + why);
+  for (int i = 0; i < 5; ++i)
+    if (r.rule_errors[i])
+      return mfail(m, PRUNE_EINVAL, "prune_model_compile: design rule " + std::to_string(i + 1) + " is violated (Sec. IV)" + why);
+  if (m->dpgs.size() != 1)
+    return mfail(m, PRUNE_EINVAL, "prune_model_compile: the runtime forms have exactly one DPG; the model has " +
+                                      std::to_string(m->dpgs.size()));
+  if (!r.consistent) return mfail(m, PRUNE_EINVAL, "prune_model_compile: the DPG is not valid and consistent (Sec. V)" + why);
+  int32_t form = 0, units = 0;
+  prune_model_classify(m, &form, &units);
+  if (form == PRUNE_FORM_NONE)
+    return mfail(m, PRUNE_EINVAL,
+                 "prune_model_compile: not a runtime form: every DC must be one static actor fed by x and feeding y, "
+                 "all with a self-loop delay (DPD) or all without (canonical)");
+  if (p->C < 1) return mfail(m, PRUNE_EINVAL, "prune_model_compile: C must be >= 1 (eq. (2))");
+  std::vector<int> roles(m->fifos.size(), -1);
+  const Dpg &d = m->dpgs[0];
+  if (form == PRUNE_FORM_CANONICAL) {
+    if (!compile_canonical(m, d, p->T, roles)) return PRUNE_EINVAL;
+    prune_graph_desc &g = out->graph;
+    g.F = units;
+    g.B = p->B;
+    g.T = p->T;
+    g.N = p->N;
+    g.C = p->C;
+    g.out_frames = p->out_frames;
+    g.tau = p->tau;
+    g.taps = p->taps;
+    g.H = p->H;
+    g.stream = p->stream;
+    g.device = p->device;
+    g.hbm_budget = p->hbm_budget;
+  } else {
+    if (!compile_dpd(m, d, roles)) return PRUNE_EINVAL;
+    if (units > 16 || p->T < 1 || p->T > 16 || p->B < 8 || p->B % 8 != 0 || p->B < p->T - 1)
+      return mfail(m, PRUNE_EINVAL, "prune_model_compile: the DPD kernel takes K <= 16 branches of 1..16 taps and "
+                                    "periods that are multiples of 8 samples, at least T-1");
+    out->dpd_K = units;
+    out->dpd_T = p->T;
+    out->dpd_period = p->B;
+  }
+  out->form = form;
+  out->units = units;
+  for (int32_t f = 0; f < n_fifos; ++f) {
+    if (f >= static_cast<int32_t>(m->fifos.size())) {
+      fifo_role[f] = -1;
+      fifo_capacity[f] = 0;
+      continue;
+    }
+    const MFifo &x = m->fifos[f];
+    fifo_role[f] = roles[f];
+    prune_fifo_capacity(x.rate, x.delay, p->C, &fifo_capacity[f]);
+  }
+  return PRUNE_OK;
+}
+
 const char *prune_model_last_error(const prune_model *m) { return m ? m->err.c_str() : "NULL model"; }
 
 }  // extern "C"

@@ -1,13 +1,13 @@
 // prune_fire_frames_noalloc: the fused firing loop for callers that cannot
 // allocate device memory.
 //
-// Who needs it: code that enqueues work while a CUDA graph is being captured
-// (cudaMalloc is not a stream operation that capture can record), real-time
-// or interrupt-driven host threads that must never block in the device
-// allocator, and deployments whose device memory is fixed up front.  Such
-// callers hand over every input and output buffer; the only other device
-// memory this entry point touches is one file-scope scratch array of fixed
-// size that the library image carries.
+// Who needs it: real-time or interrupt-driven host threads that must never
+// block in the device allocator (cudaMalloc can wait on the device and on
+// the driver's locks), and deployments whose device memory is budgeted and
+// committed up front, where an allocation at firing time may fail or is not
+// permitted at all.  Such callers hand over every input and output buffer;
+// the only other device memory this entry point touches is one file-scope
+// scratch array of fixed size that the library image carries.
 //
 // Limits and sharing:
 //   - the scratch holds up to kMaxFrames frames per call and up to kMaxLook

@@ -104,6 +104,7 @@ struct prune_graph {
   uint64_t timeout_ns = 2000000000ull;
   bool ws_loop = true;  // warp-specialised tensor-core loop (PRUNE_TC_KERNEL=pipes: tile pipelines)
   uint16_t *hx_b_ops = nullptr;       // tcgen05 B operands (N >= 64)
+  TcScale tcs{};                      // exponents of the scaled tensor-core operands (host-computed)
   uint16_t *tc_fir_ops = nullptr;     // tensor-core firing loop: FIR tap operands
   uint16_t *tc_hx_ops = nullptr;      //   and the real form of H
   int64_t cap[PRUNE_NUM_FIFOS] = {};
@@ -277,6 +278,10 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
 
 static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
   const prune_graph_desc &d = g->d;
+  if (!g->y_ring) {  // the first actor-path run of a graph that fires fused by default
+    const prune_status s = galloc(g, &g->y_ring, static_cast<size_t>(g->C) * g->L);
+    if (s != PRUNE_OK) return s;
+  }
   const int64_t T1 = std::max(d.T - 1, 1);
   FirParams fp{};
   fp.src = FrameSrc{g->f0_ring, nullptr, 0, seq0, g->C};
@@ -315,7 +320,7 @@ static prune_status run_actor_kernels(prune_graph *g, int64_t seq0, int32_t n) {
   hp.ctr = g->ctr; hp.status = g->status; hp.cap_f7 = g->cap[7];
   if (g->hx_b_ops) {
     KTimer kt(g, 4);
-    CU(g, launch_hx_tc(hp, g->hx_b_ops, g->sms, g->stream));
+    CU(g, launch_hx_tc(hp, g->hx_b_ops, g->tcs.s_h, nullptr, g->sms, g->stream));
   } else {
     KTimer kt(g, 3);
     CU(g, launch_hx_cuda(hp, hx_grid(g->sms, static_cast<int64_t>(n) * d.F), g->stream));
@@ -391,6 +396,9 @@ static prune_status run_firing_loop(prune_graph *g, int64_t seq0, int32_t n, int
     tp.lp.f.tiles = static_cast<int32_t>((g->L + kTTile - 1) / kTTile);
     tp.fir_ops = g->tc_fir_ops;
     tp.hx_ops = g->tc_hx_ops;
+    tp.s_taps = g->tcs.s_taps;
+    tp.m = g->tcs.m;
+    tp.s_h = g->tcs.s_h;
     tp.ns = tc_shifts(d.T);
     // warp-specialised loop for T <= 65 unless PRUNE_TC_KERNEL=pipes asks
     // for the tile-pipeline loop
@@ -564,9 +572,7 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
   const int32_t T = desc->T, N = desc->N;
   const size_t hist_len = static_cast<size_t>(std::max(T - 1, 1));
   if ((s = galloc(g, &g->taps, T)) || (s = galloc(g, &g->H, static_cast<size_t>(N) * N)) ||
-      (s = galloc(g, &g->stage, static_cast<size_t>(C) * L)) ||
       (s = galloc(g, &g->f0_ring, static_cast<size_t>(C))) || (s = galloc(g, &g->hist, 2 * hist_len)) ||
-      (s = galloc(g, &g->y_ring, static_cast<size_t>(C) * L)) ||
       (s = galloc(g, &g->energy, static_cast<size_t>(C) * F)) ||
       (s = galloc(g, &g->rec_c, static_cast<size_t>(out_cap))) ||
       (s = galloc(g, &g->rec_frame, static_cast<size_t>(out_cap))) ||
@@ -581,6 +587,10 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
     const long long ms = std::atoll(tm);
     if (ms > 0) g->timeout_ns = static_cast<uint64_t>(ms) * 1000000ull;
   }
+  // The staging ring (copied pushes) and the FIR output ring (the
+  // actor-per-kernel path) are allocated when first needed; a graph whose
+  // runs all take the actor path (N >= 64) gets its FIR output ring now.
+  if (!loop_supported(N) && (s = galloc(g, &g->y_ring, static_cast<size_t>(C) * L))) return bail(s);
   if (N >= 64 && hx_tc_supported(N)) {
     if ((s = galloc(g, &g->hx_b_ops, hx_tc_b_elems(N)))) return bail(s);
   }
@@ -602,8 +612,10 @@ prune_status prune_graph_create(const prune_graph_desc *desc, prune_graph **out)
             cudaMemsetAsync(g->done, 0, sizeof(uint32_t) * C, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->ready, 0, sizeof(uint64_t) * C, g->stream) == cudaSuccess &&
             cudaMemsetAsync(g->rec_c, 0, sizeof(int32_t) * out_cap, g->stream) == cudaSuccess;
-  if (ok && g->hx_b_ops) ok = hx_tc_prepare_b(g->H, N, g->hx_b_ops, g->stream) == cudaSuccess;
-  if (ok && g->tc_fir_ops) ok = tc_prepare_ops(g->taps, T, g->H, g->tc_fir_ops, g->tc_hx_ops, g->stream) == cudaSuccess;
+  g->tcs = tc_scale_of(desc->taps, T, desc->H, N);
+  if (ok && g->hx_b_ops) ok = hx_tc_prepare_b(g->H, N, g->tcs.s_h, nullptr, g->hx_b_ops, g->stream) == cudaSuccess;
+  if (ok && g->tc_fir_ops)
+    ok = tc_prepare_ops(g->taps, T, g->H, g->tcs, g->tc_fir_ops, g->tc_hx_ops, g->stream) == cudaSuccess;
   // the initial delay token of f1 is present from the start (Q = 1)
   if (ok) {
     const uint64_t init[3] = {0, 0, 1};
@@ -629,6 +641,10 @@ prune_status prune_push_frames(prune_graph *g, const void *x, int32_t n, int32_t
     return fail(g, PRUNE_EAGAIN, "f0 is full: " + std::to_string(g->pushed - g->fired) + " of " +
                                      std::to_string(g->C) + " frames waiting");
   DeviceGuard dg(g->dev);
+  if (mem != PRUNE_MEM_DEVICE_BORROW && n > 0 && !g->stage) {  // the first copied push: the staging ring
+    const prune_status s = galloc(g, &g->stage, static_cast<size_t>(g->C) * g->L);
+    if (s != PRUNE_OK) return s;
+  }
   const float2 *src = static_cast<const float2 *>(x);
   const size_t fbytes = static_cast<size_t>(g->L) * sizeof(float2);
   for (int32_t i0 = 0; i0 < n; i0 += 64) {
@@ -880,10 +896,14 @@ prune_status prune_hx(const void *y, const int32_t *idx, const int32_t *c, int32
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (N >= 64 && hx_tc_supported(N)) {
+    // H is on the device here: its exponent is found there too (a word after
+    // the operands), read by the preparation and the HX kernel
     uint16_t *bops = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&bops), hx_tc_b_elems(N) * sizeof(uint16_t), s);
-    if (e == cudaSuccess) e = hx_tc_prepare_b(hp.H, N, bops, s);
-    if (e == cudaSuccess) e = launch_hx_tc(hp, bops, sms, s);
+    e = cudaMallocAsync(reinterpret_cast<void **>(&bops), hx_tc_b_elems(N) * sizeof(uint16_t) + 16, s);
+    int32_t *sh_dev = bops ? reinterpret_cast<int32_t *>(bops + hx_tc_b_elems(N)) : nullptr;
+    if (e == cudaSuccess) e = tc_shift_of(hp.H, static_cast<int64_t>(N) * N, sh_dev, s);
+    if (e == cudaSuccess) e = hx_tc_prepare_b(hp.H, N, 0, sh_dev, bops, s);
+    if (e == cudaSuccess) e = launch_hx_tc(hp, bops, 0, sh_dev, sms, s);
     if (bops) cudaFreeAsync(bops, s);
   } else {
     e = launch_hx_cuda(hp, hx_grid(sms, static_cast<int64_t>(frames) * F), s);

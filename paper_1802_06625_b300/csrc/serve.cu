@@ -283,6 +283,9 @@ prune_status prune_server_open(prune_server *s, const prune_graph_desc *g, int64
   ss.F = g->F;
   ss.T = g->T;
   ss.tau = g->tau;
+  const TcScale sc = tc_scale_of(g->taps, g->T, g->H, N);
+  ss.s_taps = sc.s_taps;
+  ss.s_h = sc.s_h;
   ss.mem = off;
   ss.bytes = l.total;
   // through the slot's pinned staging (its previous user's copies completed
@@ -299,10 +302,11 @@ prune_status prune_server_open(prune_server *s, const prune_graph_desc *g, int64
                 cudaSuccess &&
             cudaMemsetAsync(at<int32_t>(s, ss, l.c), 0, sizeof(int32_t) * s->d.ring, s->stream) == cudaSuccess;
   if (ok && N == kTcNc)
-    ok = hx_tc_prepare_b(at<float2>(s, ss, l.H), N, at<uint16_t>(s, ss, l.bops), s->stream) == cudaSuccess;
-  if (ok && s->fir_tc) {  // block-Toeplitz tap operands (split FP16, 2^8 scale)
+    ok = hx_tc_prepare_b(at<float2>(s, ss, l.H), N, sc.s_h, nullptr, at<uint16_t>(s, ss, l.bops), s->stream) ==
+         cudaSuccess;
+  if (ok && s->fir_tc) {  // block-Toeplitz tap operands (split FP16, scaled by 2^s_taps)
     tc_prepare_fir_kernel<<<dim3(64, tc_shifts(g->T)), 64, 0, s->stream>>>(at<float2>(s, ss, l.taps), g->T,
-                                                                            at<uint16_t>(s, ss, l.fops));
+                                                                            sc.s_taps, at<uint16_t>(s, ss, l.fops));
     ok = cudaGetLastError() == cudaSuccess;
   }
   if (!ok) {
@@ -380,6 +384,8 @@ prune_status prune_server_step(prune_server *s, int32_t *entries) {
     in.T = ss.T;
     in.TP = fir_taps_padded(ss.T);
     in.tau = ss.tau;
+    in.s_taps = ss.s_taps;
+    in.s_h = ss.s_h;
     in.fir_tile0 = nfir;
     in.hx_tile0 = nhx;
     const int64_t tiles = (L + s->TS - 1) / s->TS, items = hx_items_of(ss.F, B, N);

@@ -134,6 +134,7 @@ struct StreamState {
   int64_t id = 0;
   int32_t F = 0, T = 0;
   float tau = 0.f;
+  int32_t s_taps = 0, s_h = 0;   // exponents of the scaled tensor-core operands
   uint64_t mem = 0, bytes = 0;   // arena block
   std::deque<Segment> queue;
   int64_t queued = 0;            // frames submitted and not yet fired

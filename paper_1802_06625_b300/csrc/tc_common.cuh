@@ -7,7 +7,16 @@
 // outputs of row m are y_m = sum_{s=0}^{S} G_s X_{m-s}, S = ceil((T-1)/32),
 // X_j the j-th 32-sample input chunk from the tile start: the convolution
 // y[n] = sum_t h[t] x[n-t] regrouped.  Each G_s is used in its real form
-// (64 x 64) split into FP16 hi and lo parts, pre-scaled by 2^8.
+// (64 x 64) split into FP16 hi and lo parts.
+//
+// Range.  FP16 holds magnitudes in [2^-14, 65504] at full precision, FP32
+// far more, so every operand is scaled by a power of two (exact) before it
+// is split (tc_scale.cuh): the taps and H once per graph, each input tile
+// (with its halo) by the exponent its largest component needs, and the FIR
+// output by a per-graph 2^m from the L1 bound of the taps so that the HX
+// operand stays below 2^14.  Results are scaled back in the epilogues (again
+// exact), so the split keeps ~2^-21 relative precision independent of the
+// signal's level.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -24,8 +33,6 @@ constexpr int kTMaxPieces = (kTGroups + kTMaxShifts - 1) * 64 / 256;  // per thr
 constexpr uint32_t kTOpBytes = 64 * 128; // one 64 x 64 FP16 operand (8 KB)
 constexpr uint32_t kTIdescN64 = (1u << 4) | (static_cast<uint32_t>(64 >> 3) << 17) |
                                 (static_cast<uint32_t>(kTRows >> 4) << 24);
-constexpr float kTScale = 256.f;
-
 __host__ __device__ inline int tc_shifts(int T) { return 1 + (T - 1 + kTR - 1) / kTR; }
 
 constexpr uint32_t kTIdescN128 = (1u << 4) | (static_cast<uint32_t>(128 >> 3) << 17) |
@@ -41,8 +48,8 @@ __device__ __forceinline__ float real_form(float2 g, int n, int k) {
   return (k & 1) == 0 ? g.y : g.x;
 }
 
+// v (already scaled) as FP16 hi = fp16(v) and lo = fp16(v - hi).
 __device__ __forceinline__ void store_split(uint16_t *ops, uint32_t half_elems, int n, int k, float v) {
-  v *= kTScale;
   const __half hi = __float2half_rn(v);
   const __half lo = __float2half_rn(v - __half2float(hi));
   const uint32_t off = sw128_off(n, k, 64) >> 1;
@@ -50,25 +57,26 @@ __device__ __forceinline__ void store_split(uint16_t *ops, uint32_t half_elems, 
   ops[half_elems + off] = __half_as_ushort(lo);
 }
 
-// FIR operands: shift s, real row n < 64 (output 2i+a), real column k < 64.
-static __global__ void tc_prepare_fir_kernel(const float2 *taps, int T, uint16_t *ops) {
+// FIR operands: shift s, real row n < 64 (output 2i+a), real column k < 64,
+// of the taps scaled by 2^sh (TcScale::s_taps).
+static __global__ void tc_prepare_fir_kernel(const float2 *taps, int T, int sh, uint16_t *ops) {
   const int s = blockIdx.y, n = blockIdx.x, k = threadIdx.x;
   const int i = n >> 1, u = k >> 1;
   const int t = i - u + kTR * s;
   const float2 g = (t >= 0 && t < T) ? taps[t] : make_float2(0.f, 0.f);
-  store_split(ops + static_cast<size_t>(s) * 2 * 64 * 64, 64 * 64, n, k, real_form(g, n, k));
+  store_split(ops + static_cast<size_t>(s) * 2 * 64 * 64, 64 * 64, n, k, real_form(g, n, k) * exp2i(sh));
 }
 
-// HX operands: real form of H (32 x 32 complex).
-static __global__ void tc_prepare_hx_kernel(const float2 *H, uint16_t *ops) {
+// HX operands: real form of H (32 x 32 complex) scaled by 2^sh (TcScale::s_h).
+static __global__ void tc_prepare_hx_kernel(const float2 *H, int sh, uint16_t *ops) {
   const int n = blockIdx.x, k = threadIdx.x;
-  store_split(ops, 64 * 64, n, k, real_form(H[(n >> 1) * kTR + (k >> 1)], n, k));
+  store_split(ops, 64 * 64, n, k, real_form(H[(n >> 1) * kTR + (k >> 1)], n, k) * exp2i(sh));
 }
 
-__host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const float2 *H, uint16_t *fir_ops,
-                                           uint16_t *hx_ops, cudaStream_t s) {
-  tc_prepare_fir_kernel<<<dim3(64, tc_shifts(T)), 64, 0, s>>>(taps, T, fir_ops);
-  tc_prepare_hx_kernel<<<64, 64, 0, s>>>(H, hx_ops);
+__host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const float2 *H, const TcScale &sc,
+                                           uint16_t *fir_ops, uint16_t *hx_ops, cudaStream_t s) {
+  tc_prepare_fir_kernel<<<dim3(64, tc_shifts(T)), 64, 0, s>>>(taps, T, sc.s_taps, fir_ops);
+  tc_prepare_hx_kernel<<<64, 64, 0, s>>>(H, sc.s_h, hx_ops);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,21 @@ class Graph:
         self.h = h
         self._borrowed = []   # keep borrowed frames alive until fired
 
+    @classmethod
+    def from_desc(cls, desc):
+        """A graph made by prune_graph_create from a filled prune_graph_desc
+        (e.g. the one prune_model_compile writes)."""
+        g = cls.__new__(cls)
+        g.F, g.B, g.T, g.N, g.C = desc.F, desc.B, desc.T, desc.N, desc.C
+        g.L = desc.F * desc.B
+        g.device = desc.device if desc.device >= 0 else torch.cuda.current_device()
+        g.stream = None
+        h = ctypes.c_void_p()
+        check(_lib.lib().prune_graph_create(ctypes.byref(desc), ctypes.byref(h)))
+        g.h = h
+        g._borrowed = []
+        return g
+
     def close(self):
         if getattr(self, "h", None):
             _lib.lib().prune_graph_destroy(self.h)

@@ -1,10 +1,13 @@
 """Python view of the graph front end (prune_model_*): describe a PRUNE
 graph, run the compile-time analysis (rates, actor types, design rules 1-5,
-DPGs, DCs, validity, consistency, buffer bounds) and classify it against the
-forms the runtime fires.  Argument marshalling only; host code, no device."""
+DPGs, DCs, validity, consistency, buffer bounds), classify it against the
+forms the runtime fires and compile it into one of them.  Argument
+marshalling only; host code, no device."""
 from __future__ import annotations
 
 import ctypes
+
+import numpy as np
 
 from . import _lib
 from ._lib import check
@@ -94,3 +97,34 @@ class Model:
         f, u = ctypes.c_int32(), ctypes.c_int32()
         self._c(_lib.lib().prune_model_classify(self.h, ctypes.byref(f), ctypes.byref(u)))
         return FORMS[f.value], u.value
+
+    def compile(self, B, T, N=1, C=3, tau=0.0, taps=None, H=None, out_frames=0, device=-1, hbm_budget=0):
+        """prune_model_compile: the runtime form of the checked model.
+        Returns a dict: form ("canonical" or "dpd"), units, roles (runtime
+        FIFO of every model FIFO), capacities (eq. (2) tokens) and, for the
+        canonical form, desc (the prune_graph_desc, whose host arrays it
+        keeps alive) or, for DPD, K, T and period.  Raises PruneError with
+        the reason for any other model."""
+        p = _lib.prune_compile_params(B=B, T=T, N=N, C=C, tau=float(tau), out_frames=out_frames, device=device,
+                                      hbm_budget=hbm_budget)
+        keep = []
+        if taps is not None:
+            t = np.ascontiguousarray(np.asarray(taps, np.complex64)).view(np.float32).reshape(-1)
+            keep.append(t)
+            p.taps = t.ctypes.data
+        if H is not None:
+            h = np.ascontiguousarray(np.asarray(H, np.complex64)).view(np.float32).reshape(-1)
+            keep.append(h)
+            p.H = h.ctypes.data
+        out = _lib.prune_compiled()
+        n = len(self.fifos)
+        roles = (ctypes.c_int32 * max(n, 1))()
+        caps = (ctypes.c_int64 * max(n, 1))()
+        self._c(_lib.lib().prune_model_compile(self.h, ctypes.byref(p), ctypes.byref(out), roles, caps, n))
+        r = {"form": FORMS[out.form], "units": out.units, "roles": list(roles[:n]), "capacities": list(caps[:n])}
+        if out.form == 1:
+            r["desc"] = out.graph
+            r["_keep"] = keep
+        else:
+            r.update(K=out.dpd_K, T=out.dpd_T, period=out.dpd_period)
+        return r

@@ -1,0 +1,157 @@
+"""Control of every frame and every instance of the full-size workloads the
+bench times, against the oracle.
+
+- Plain large (1000 frames of 4096 blocks x 1024 samples, T = 64, N = 32):
+  fired exactly as the bench fires it (frames resident on the device, pushed
+  by reference in runs of C = 336, the warp-specialised tensor-core loop).
+  The oracle fires every frame on the host, in frame ranges spread over
+  spawned worker processes (each range is fed the tail of the frame before
+  it as its delay token).  c and idx of all 1000 frames are compared
+  bit-exactly outside the guard band; the samples are checked on sampled
+  frames elsewhere.
+- Batched (one step of the 512 uneven instances, N = 64, tensor-core FIR
+  and HX replayed as one CUDA graph): c and idx of every instance against
+  the oracle, and the samples of every instance within the tolerance.
+
+The number of blocks whose oracle energy lies in the guard band is reported
+per workload (printed; pytest -s shows it).
+"""
+import ctypes
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from parity import TOL_REL, compare_frame, in_band
+from paper_1802_06625_b300 import synth
+
+import oracle_ranges
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _workers():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def _check_control(c_g, idx_g, c_o, idx_o, energy_o, tau, F):
+    """Decisions outside the band equal; idx ascending; everything equal when
+    no block is in the band.  Returns the number of in-band blocks."""
+    band = in_band(energy_o, tau)
+    idx_g = np.asarray(idx_g)[:c_g]
+    assert np.all(np.diff(idx_g) > 0)
+    sel_g = np.zeros(F, bool)
+    sel_g[idx_g] = True
+    sel_o = np.zeros(F, bool)
+    sel_o[np.asarray(idx_o)] = True
+    assert np.array_equal(sel_g[~band], sel_o[~band]), "decisions differ outside the guard band"
+    if not band.any():
+        assert c_g == c_o and np.array_equal(idx_g, idx_o)
+    return int(band.sum())
+
+
+def test_plain_large_every_frame_control_against_oracle():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1802_06625_b300 import _lib
+    from paper_1802_06625_b300.graph import Graph
+
+    w = synth.PLAIN_LARGE
+    n, C = w.frames, 336
+    # the oracle's frame ranges start first, in spawned processes, and run
+    # while the GPU fires the stream
+    nw = _workers()
+    bounds = np.linspace(0, n, 4 * nw + 1).astype(int)
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(nw)
+    pending = pool.map_async(oracle_ranges.plain_range, list(zip(bounds[:-1], bounds[1:])))
+
+    dev = torch.device("cuda", 0)
+    x = torch.empty(n, w.F, w.B, dtype=torch.complex64, device=dev)
+    for k in range(n):
+        x[k] = w.frame(k, device=dev)
+    g = Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=C, out_frames=C, device=0)
+    lib = _lib.lib()
+    ch = 16
+    idx_d = torch.empty(ch, w.F, dtype=torch.int32, device=dev)
+    y_d = torch.empty(ch, w.F * w.B, dtype=torch.complex64, device=dev)
+    recs = (_lib.prune_frame_out * ch)()
+    got_c = np.zeros(n, np.int64)
+    got_idx = [None] * n
+    for k0 in range(0, n, C):
+        m = min(C, n - k0)
+        g.push(x[k0:k0 + m], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+        assert g.run() == m
+        done = 0
+        while done < m:
+            q = min(ch, m - done)
+            for i in range(q):
+                recs[i].idx = idx_d[i].data_ptr()
+                recs[i].y = y_d[i].data_ptr()
+            cnt = ctypes.c_int32()
+            _lib.check(lib.prune_pull(g.h, recs, q, ctypes.byref(cnt), _lib.PRUNE_MEM_DEVICE), g.h)
+            assert cnt.value == q
+            ih = idx_d[:q].cpu().numpy()
+            for i in range(q):
+                k = recs[i].frame
+                assert k == k0 + done + i
+                got_c[k] = recs[i].c
+                got_idx[k] = ih[i, :recs[i].c].copy()
+            done += q
+    g.close()
+    del x, y_d
+
+    results = [r for part in pending.get(timeout=3600) for r in part]
+    pool.close()
+    pool.join()
+    assert [r[0] for r in results] == list(range(n))
+    tau = np.float32(w.tau)
+    band = 0
+    for k, c_o, idx_o, e_o in results:
+        band += _check_control(int(got_c[k]), got_idx[k], c_o, idx_o, e_o, tau, w.F)
+    print(f"plain large: {n} frames, control equal to the oracle's; in-band blocks: {band}")
+    assert got_c.sum() > 0
+
+
+def test_batched_every_instance_against_oracle():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1802_06625_b300.graph import Batch
+
+    b = synth.BATCHED
+    nw = _workers()
+    ids = list(range(b.instances))
+    parts = [ids[i::4 * nw] for i in range(4 * nw)]
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(nw)
+    pending = pool.map_async(oracle_ranges.batched_instances, parts)
+
+    ws = [b.instance(i) for i in ids]
+    dev = torch.device("cuda", 0)
+    x = torch.cat([w.frame(0, device=dev).reshape(-1) for w in ws])
+    bt = Batch(b.B, b.N, [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws], device=0)
+    bt.autotune(x, reps=1)
+    bt.fire(x, graph=True)
+    bt.sync()
+    got = [bt.pull(i) for i in ids]
+    bt.close()
+
+    results = {r[0]: r[1:] for part in pending.get(timeout=3600) for r in part}
+    pool.close()
+    pool.join()
+    band_by_T = {}
+    worst = 0.0
+    for i, w in enumerate(ws):
+        c_o, idx_o, e_o, y_o = results[i]
+        frame, c, idx, y = got[i]
+        tau = np.float32(w.tau)
+        nb = _check_control(int(c), np.asarray(idx)[:c], c_o, idx_o, e_o, tau, w.F)
+        band_by_T[w.T] = band_by_T.get(w.T, 0) + nb
+        err, rms, _ = compare_frame(c, np.asarray(idx)[:c], np.asarray(y)[:c], c_o, idx_o, y_o, e_o, tau, b.B)
+        if rms > 0:
+            worst = max(worst, err / rms)
+    assert worst <= TOL_REL, worst
+    print(f"batched: {b.instances} instances, control equal to the oracle's, samples within "
+          f"{worst:.2e} x RMS; in-band blocks by T: {band_by_T}")

@@ -327,3 +327,35 @@ def test_plain_large_host_frames_in_chunks_sampled(G):
         frame, c, idx, y = recs[s]
         err, rms, nb = compare_frame(c, idx, y, r.c[-1], r.idx[-1], r.y[-1], r.energy[-1], np.float32(w.tau), w.B)
         assert rms > 0 and err <= TOL_REL * rms, (s, err / rms, nb)
+
+
+def test_staging_and_fir_rings_are_allocated_only_when_needed(G):
+    # F = 4096, B = 1024, C = 16: each C-frame ring is 16 x 32 MiB = 512 MiB.
+    # The fused graph fed by borrowed pushes needs only its result ring (and
+    # small state); the staging ring comes with the first copied push, the
+    # FIR output ring with the first actor-path run, each against the budget.
+    from paper_1802_06625_b300 import _lib
+
+    w = synth.PlainWorkload("lazy", F=4096, B=1024, T=64, N=32, frames=2, tau=4096.0, seed=8, p=0.3)
+    x = w.frames_tensor(0, 2).cuda()
+    ring = 16 * w.F * w.B * 8
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=16, out_frames=16,
+                hbm_budget=ring + (64 << 20))
+    g.push(x[:1], mem=_lib.PRUNE_MEM_DEVICE_BORROW)
+    assert g.run(sync=True) == 1
+    with pytest.raises(_lib.PruneError) as e:
+        g.push(x[1:])                                   # a copied push: the staging ring does not fit
+    assert e.value.status == _lib.PRUNE_ENOMEM
+    g.push(x[1:], mem=_lib.PRUNE_MEM_DEVICE_BORROW)     # nothing changed: borrowed pushes still work
+    with pytest.raises(_lib.PruneError) as e:
+        g.run(actors=True)                              # the actor path's FIR ring does not fit either
+    assert e.value.status == _lib.PRUNE_ENOMEM
+    assert g.run(sync=True) == 1
+    assert [r[0] for r in g.pull()] == [0, 1]
+    g.close()
+    # with room for one more ring, the copied push succeeds
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=16, out_frames=16,
+                hbm_budget=2 * ring + (64 << 20))
+    g.push(x)
+    assert g.run(sync=True) == 2
+    g.close()

@@ -5,6 +5,8 @@ decompositions, validity, consistency and buffer bounds agree, and the
 runtime forms are recognised."""
 import random
 
+import numpy as np
+
 import pytest
 
 from oracle import analysis as A
@@ -253,3 +255,75 @@ def test_random_graphs(seed):
 @pytest.mark.parametrize("seed", range(200))
 def test_random_valid_graphs(seed):
     compare(clean_graph(seed))
+
+
+# ---------------------------------------------------------------- compile
+
+def _canonical_model(F, **kw):
+    return to_model(A.canonical_graph(F, **kw))
+
+
+@pytest.mark.parametrize("F", [1, 3, 64])
+def test_compile_canonical_fills_the_graph_descriptor(F):
+    import oracle
+    m = _canonical_model(F)
+    r = m.compile(B=256, T=16, N=16, C=3, tau=1024.0, taps=np.ones(16, np.complex64),
+                  H=np.eye(16, dtype=np.complex64), out_frames=5)
+    assert r["form"] == "canonical" and r["units"] == F
+    d = r["desc"]
+    assert (d.F, d.B, d.T, d.N, d.C, d.out_frames) == (F, 256, 16, 16, 3, 5)
+    assert abs(d.tau - 1024.0) < 1e-6 and d.taps and d.H
+    # every model FIFO has its runtime FIFO and its eq. (2) capacity
+    g = A.canonical_graph(F)
+    names = [f.name for f in g.fifos]
+    want = {"f0": 0, "f1": 1, "f2": 2, "f3": 3, "f4": 4, "f5": 5}
+    for fi, name in enumerate(names):
+        role = want.get(name, 6 if name.startswith("f6_") else 7)
+        assert r["roles"][fi] == role, (name, r["roles"][fi])
+        assert r["capacities"][fi] == oracle.fifo_capacity(g.fifos[fi].rate, g.fifos[fi].delay, 3)
+
+
+@pytest.mark.parametrize("K", [1, 4, 10])
+def test_compile_dpd_fills_the_dpd_arguments(K):
+    m = to_model(A.dpd_graph(K))
+    r = m.compile(B=4096, T=10, C=3)
+    assert (r["form"], r["units"], r["K"], r["T"], r["period"]) == ("dpd", K, K, 10, 4096)
+    names = [f.name for f in A.dpd_graph(K).fifos]
+    roles = dict(zip(names, r["roles"]))
+    assert roles["fx"] == 0 and roles["fcfg"] == 1 and roles["fcp"] == 5 and roles["fca"] == 5 and roles["fy"] == 6
+    assert all(roles[f"fp_{k}"] == 2 and roles[f"fh_{k}"] == 3 and roles[f"ff_{k}"] == 4 for k in range(K))
+
+
+def _rejected(m, **kw):
+    from paper_1802_06625_b300._lib import PruneError
+    args = dict(B=256, T=16, N=16, C=3, tau=1.0, taps=np.ones(16, np.complex64), H=np.eye(16, dtype=np.complex64))
+    args.update(kw)
+    with pytest.raises(PruneError) as e:
+        m.compile(**args)
+    return str(e.value)
+
+
+def test_compile_rejects_rule_violations_with_the_rule():
+    assert "design rule 1" in _rejected(_canonical_model(3, swap_sink_elements=(0, 2)))
+    assert "design rule 2" in _rejected(_canonical_model(2, delay_f4=1))
+
+
+def test_compile_rejects_graphs_outside_the_runtime_forms():
+    # the Fig. 5 example: a valid PRUNE graph, but not a form the runtime fires
+    msg = _rejected(to_model(T._fig5_graph()))
+    assert "not a runtime form" in msg or "DPG" in msg, msg
+    # a canonical graph whose FIR keeps two delay tokens
+    g = A.canonical_graph(3)
+    for f in g.fifos:
+        if f.name == "f1":
+            f.delay = 2
+    assert "delay line" in _rejected(to_model(g))
+    # a canonical graph whose FIR has no delay line, with T > 1
+    g = A.canonical_graph(3)
+    g.fifos = [f for f in g.fifos if f.name != "f1"]
+    g.ports = {k: p for k, p in g.ports.items() if not (p.actor == "FIR" and p.name in ("hin", "hout"))}
+    assert "no self-loop" in _rejected(to_model(g), T=16)
+    # DPD limits of the kernel (17 branches)
+    assert "DPD kernel" in _rejected(to_model(A.dpd_graph(17)), B=4096, T=10)
+    # C must be positive (eq. (2))
+    assert "C must be" in _rejected(_canonical_model(2), C=0)
