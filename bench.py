@@ -41,7 +41,7 @@ METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 lat
 # the warp-specialised loop, dram__bytes_read.sum + dram__bytes_write.sum
 # divided by 48); scaled to a launch by the frames it fires.  Remove an entry
 # when its kernel changes.
-TRAFFIC_PER_FRAME = {6: (1611.613e6 + 812.035e6) / 48}
+TRAFFIC_PER_FRAME = {}
 UNIT = "Msamples/s"
 # FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
 # FP32 lanes x 2 flop x 2.032 GHz.

@@ -4,6 +4,7 @@
 // Instances are independent DPGs (Sec. V), so the batch is a union of
 // graphs; every instance keeps its own delay token across steps.
 #pragma once
+#include <type_traits>
 #include <algorithm>
 
 #include "batch_fir_tc.cuh"
@@ -213,7 +214,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 132);
   BhxRec *rec = reinterpret_cast<BhxRec *>(misc + 256);      // [2]
   int32_t *s_tile = reinterpret_cast<int32_t *>(misc + 1024); // [2] the tile's exponent per stage
-  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 1088); // [8] work warps' largest |x|
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 1088); // [2 stages][2][8] work warps' maxima
   float *xpose = reinterpret_cast<float *>(misc + kBhxMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int RB = bp.B / kTcNc;                                // rows per block
@@ -258,7 +259,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
     int issued = 0;
     for (int i = 0; i < cnt; ++i) {
       const int st = i & 1;
-      if (i >= 2 && !ws_wait(smem_u32(&st_free[st]), ((i >> 1) - 1) & 1, bp.timeout_ns, stop)) {
+      if (i >= 2 && !__all_sync(0xffffffffu, ws_wait(smem_u32(&st_free[st]), ((i >> 1) - 1) & 1, bp.timeout_ns, stop))) {
         if (lane == 0) fail(24);
         break;
       }
@@ -331,6 +332,7 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
     int loaded = -1;
     uint32_t b_par = 0;
     bool reload_open = false;  // an R copy issued and not yet seen to land
+    int sx_pred = 0;           // scale exponent of the previous tile
     auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
       const bool w = mbar_wait_bounded(smem_u32(mb), par, bp.timeout_ns);
       return bf_bar_and(w && !*stop);
@@ -427,38 +429,44 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
           u[k][1] = u[k][0];
         }
       }
-      {
-        float mx = 0.f;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k)
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
-        const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-        if (lane == 0) cred[warp] = wm;
-      }
       bf_bar();
-      uint32_t tmx = cred[0];
-#pragma unroll
-      for (int w = 1; w < 8; ++w) tmx = max(tmx, cred[w]);
-      const int sx = tc_shift_bits(tmx);
-      if (tid == 0) s_tile[st] = sx;
-      if (sx != 0) {  // uniform
-        const float sc = exp2i(sx);
+      auto split_all = [&](int sxc) -> uint32_t {
+        const float sc = exp2i(sxc);
+        uint32_t hm = 0u;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
-          u[k][0].x *= sc; u[k][0].y *= sc; u[k][0].z *= sc; u[k][0].w *= sc;
-          u[k][1].x *= sc; u[k][1].y *= sc; u[k][1].z *= sc; u[k][1].w *= sc;
-        }
-      }
+          const int q = tid + k * kTcThreads;
+          const int m = q >> 4, cc = q & 15;
+          float v[8] = {u[k][0].x, u[k][0].y, u[k][0].z, u[k][0].w, u[k][1].x, u[k][1].y, u[k][1].z, u[k][1].w};
+          // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
 #pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const int q = tid + k * kTcThreads;
-        const int m = q >> 4, cc = q & 15;
-        const float v[8] = {u[k][0].x, u[k][0].y, u[k][0].z, u[k][0].w, u[k][1].x, u[k][1].y, u[k][1].z, u[k][1].w};
-        const uint32_t off = sw128_off(m, cc * 8, kTcM);
-        *reinterpret_cast<uint4 *>(stg + off) = split_pack(v, false);
-        *reinterpret_cast<uint4 *>(stg + kTcOpBytes + off) = split_pack(v, true);
+          for (int e = 0; e < 8; ++e) v[e] *= sc;
+          uint4 h4, l4;
+          split_pair(v[0], v[1], h4.x, l4.x);
+          split_pair(v[2], v[3], h4.y, l4.y);
+          split_pair(v[4], v[5], h4.z, l4.z);
+          split_pair(v[6], v[7], h4.w, l4.w);
+          hmax_abs_acc(hm, h4.x);
+          hmax_abs_acc(hm, h4.y);
+          hmax_abs_acc(hm, h4.z);
+          hmax_abs_acc(hm, h4.w);
+          const uint32_t off = sw128_off(m, cc * 8, kTcM);
+          *reinterpret_cast<uint4 *>(stg + off) = h4;
+          *reinterpret_cast<uint4 *>(stg + kTcOpBytes + off) = l4;
+        }
+        return hm;
+      };
+      // the tile scaled by 2^sx, sx predicted from the previous tile (none
+      // when it is 0); the largest FP16 hi part, exchanged through the
+      // barrier that ends the conversion, gives the tile's own exponent, and
+      // a tile whose own exponent differs is split once more from the
+      // registers (uniform, rare)
+      uint32_t *cr = cred + st * 16;  // [stage][hi max, FP32 max][8 warps]
+      int sx = sx_pred;
+      {
+        const uint32_t hm = split_all(sx);
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax_abs_bits(hm));
+        if (lane == 0) cr[warp] = wm;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {
@@ -468,6 +476,35 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
         reload_open = false;
       } else {
         bf_bar();
+      }
+      {
+        uint32_t h16 = cr[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) h16 = max(h16, cr[w]);
+        int own = tc_shift_from_hi(h16, sx);
+        if (own == -1000) {  // zero, subnormal or inf hi parts: the FP32 maximum decides
+          float mx = 0.f;
+#pragma unroll
+          for (int k = 0; k < kPer; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
+          const uint32_t fm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+          if (lane == 0) cr[8 + warp] = fm;
+          bf_bar();
+          uint32_t f32 = cr[8];
+#pragma unroll
+          for (int w = 1; w < 8; ++w) f32 = max(f32, cr[8 + w]);
+          own = tc_shift_bits(f32);
+        }
+        if (own != sx) {
+          sx = own;
+          split_all(sx);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bf_bar();
+        }
+        sx_pred = sx;
+        if (tid == 0) s_tile[st] = sx;
       }
       if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
       if (i >= 1) {  // tile i-1's accumulator, read back while tile i's GEMMs run

@@ -35,6 +35,8 @@
 // The issuing thread commits once more to a barrier of its own and waits
 // before tensor memory is freed.
 #pragma once
+#include <type_traits>
+
 #include "batch_partition.hpp"
 #include "batch_types.cuh"
 #include "tc_common.cuh"
@@ -93,6 +95,7 @@ struct BfRec {
   int32_t inst, nv, S, T;
   int32_t s_taps, sx;   // the taps' exponent, the tile's (set by the converter)
 };
+static_assert(sizeof(BfRec) <= 80, "the misc layout holds 3 + 4 records of at most 80 bytes");
 
 static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(BatchParams bp) {
   extern __shared__ unsigned char smem_raw[];
@@ -110,12 +113,15 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
   uint64_t *acc_empty = mma_done + kBfAccs;                  // [4] accumulator a read back
   uint64_t *fin = acc_empty + kBfAccs;                       // the issuer's last commit, at exit
   uint64_t *b_full = fin + 1;                                // an instance's tap operands landed
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 168);
-  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 172);
-  BfRec *rec = reinterpret_cast<BfRec *>(misc + 192);        // [3] per stage
-  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 448); // [8] converter warps' largest |x|
+  // misc: barriers [0, 152), tmem slot, stop flag, records [176, 416),
+  // row energies [512, 1536), accumulator records [1536, 1856), converter
+  // maxima [1856, 2048)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 160);
+  volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 164);
+  BfRec *rec = reinterpret_cast<BfRec *>(misc + 176);        // [3] per stage
   float *eth = reinterpret_cast<float *>(misc + 512);        // [2][128] row energies per column half
   BfRec *acc_rec = reinterpret_cast<BfRec *>(misc + 1536);   // [4] per accumulator
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 1856);  // [3 stages][2][8] converter warps' maxima
   float *xpose = reinterpret_cast<float *>(misc + kBfMiscBytes);  // [8 warps][32 rows][16 floats]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = bp.fir_cta ? bp.fir_cta[blockIdx.x]
@@ -151,7 +157,8 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     int issued = 0;
     for (int i = 0; i < n; ++i) {
       const int st = i % kBfStages;
-      if (i >= kBfStages && !ws_wait(smem_u32(&st_free[st]), ((i / kBfStages) - 1) & 1, bp.timeout_ns, stop)) {
+      if (i >= kBfStages &&
+          !__all_sync(0xffffffffu, ws_wait(smem_u32(&st_free[st]), ((i / kBfStages) - 1) & 1, bp.timeout_ns, stop))) {
         if (lane == 0) fail(23, 0);
         break;
       }
@@ -254,6 +261,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
     int loaded = -1;
     uint32_t b_par = 0;
     bool reload_open = false;  // a tap copy issued and not yet seen to land
+    int sx_pred = 0;           // scale exponent of the group's previous tile
     // bounded wait by every thread of the group, outcome combined
     auto wait_all = [&](uint64_t *mb, uint32_t par) -> bool {
       const bool w = ws_wait(smem_u32(mb), par, bp.timeout_ns, stop);
@@ -308,44 +316,50 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       if (r.hout && r.s0 + nv == r.L)
         for (int m = tid; m < r.T - 1; m += kBfWork)
           r.hout[m] = reinterpret_cast<const float2 *>(stg)[kBfRawHalo + nv - (r.T - 1) + m];
-      // the tile's scale: its largest component (halo included)
-      {
-        float mx = 0.f;
-#pragma unroll
-        for (int k = 0; k < kBfMaxPieces; ++k)
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
-        const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-        if (lane == 0) cred[warp] = wm;
-      }
-      bar256<1>();  // every raw sample of the stage has been read, every warp's largest |x| is in cred
-      uint32_t tm = cred[0];
-#pragma unroll
-      for (int w = 1; w < 8; ++w) tm = max(tm, cred[w]);
-      const int sx = tc_pow2_shift(__uint_as_float(tm));
-      const float xsc = exp2i(sx);
+      bar256<1>();  // every raw sample of the stage has been read
+      // the tile as the split-FP16 chunk array, scaled by 2^sx, sx predicted
+      // from this group's previous tile (no multiply when it is 0); the
+      // largest FP16 hi part, exchanged through the barrier that ends the
+      // conversion, gives the tile's own exponent, and a tile whose own
+      // exponent differs is split once more from the registers (uniform,
+      // rare): the exponent a tile is fired with depends on the tile alone
       unsigned char *ahi = stg, *alo = stg + (kTGroups + S) * 1024;
+      auto split_all = [&](int sxc) -> uint32_t {
+        const float xsc = exp2i(sxc);
+        uint32_t hm = 0u;
 #pragma unroll
-      for (int k = 0; k < kBfMaxPieces; ++k) {
-        const int q = tid + kBfWork * k;
-        if (q < npieces) {
-          const int row = q >> 3, pc = q & 7;
-          const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-          if (sx != 0) {  // uniform
-            u[k][0].x *= xsc; u[k][0].y *= xsc; u[k][0].z *= xsc; u[k][0].w *= xsc;
-            u[k][1].x *= xsc; u[k][1].y *= xsc; u[k][1].z *= xsc; u[k][1].w *= xsc;
+        for (int k = 0; k < kBfMaxPieces; ++k) {
+          const int q = tid + kBfWork * k;
+          if (q < npieces) {
+            const int row = q >> 3, pc = q & 7;
+            const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+            float4 a = u[k][0], c = u[k][1];
+            // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
+            a.x *= xsc; a.y *= xsc; a.z *= xsc; a.w *= xsc;
+            c.x *= xsc; c.y *= xsc; c.z *= xsc; c.w *= xsc;
+            uint4 h4, l4;
+            split_pair(a.x, a.y, h4.x, l4.x);
+            split_pair(a.z, a.w, h4.y, l4.y);
+            split_pair(c.x, c.y, h4.z, l4.z);
+            split_pair(c.z, c.w, h4.w, l4.w);
+            hmax_abs_acc(hm, h4.x);
+            hmax_abs_acc(hm, h4.y);
+            hmax_abs_acc(hm, h4.z);
+            hmax_abs_acc(hm, h4.w);
+            *reinterpret_cast<uint4 *>(ahi + off) = h4;
+            *reinterpret_cast<uint4 *>(alo + off) = l4;
           }
-          uint4 h4, l4;
-          split_pair(u[k][0].x, u[k][0].y, h4.x, l4.x);
-          split_pair(u[k][0].z, u[k][0].w, h4.y, l4.y);
-          split_pair(u[k][1].x, u[k][1].y, h4.z, l4.z);
-          split_pair(u[k][1].z, u[k][1].w, h4.w, l4.w);
-          *reinterpret_cast<uint4 *>(ahi + off) = h4;
-          *reinterpret_cast<uint4 *>(alo + off) = l4;
         }
+        return hm;
+      };
+      // cred: [stage][hi max of pass 0, FP32 max][8 warps]
+      uint32_t *cr = cred + st * 16;
+      int sx = sx_pred;
+      {
+        const uint32_t hm = split_all(sx);
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax_abs_bits(hm));
+        if (lane == 0) cr[warp] = wm;
       }
-      if (tid == 0) rec[st].sx = sx;  // read by the MMA warp after a_full
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (reload) {  // the tap operands (copied while the tile was converted)
         ok = wait_all(b_full, b_par);
@@ -355,6 +369,35 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       } else {
         bar256<1>();
       }
+      {
+        uint32_t h16 = cr[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) h16 = max(h16, cr[w]);
+        int own = tc_shift_from_hi(h16, sx);
+        if (own == -1000) {  // zero, subnormal or inf hi parts: the FP32 maximum decides
+          float mx = 0.f;
+#pragma unroll
+          for (int k = 0; k < kBfMaxPieces; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[k][h].x), fabsf(u[k][h].y)), fmaxf(fabsf(u[k][h].z), fabsf(u[k][h].w))));
+          const uint32_t fm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+          if (lane == 0) cr[8 + warp] = fm;
+          bar256<1>();
+          uint32_t f32 = cr[8];
+#pragma unroll
+          for (int w = 1; w < 8; ++w) f32 = max(f32, cr[8 + w]);
+          own = tc_shift_bits(f32);
+        }
+        if (own != sx) {
+          sx = own;
+          split_all(sx);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar256<1>();
+        }
+        sx_pred = sx;
+      }
+      if (tid == 0) rec[st].sx = sx;  // read by the MMA warp after a_full
       if (tid == 0) mbar_arrive(smem_u32(&a_full[st]));
     }
     // a tap reload whose copy was not seen to land (the group left on a

@@ -33,6 +33,8 @@
 // tc_ticket_tile); the last tile of a frame writes the SINK record and books the FIFO counters in frame order.  All waits are
 // bounded; tensor memory is freed on every path.
 #pragma once
+#include <type_traits>
+
 #include "firing_loop.cuh"
 #include "tc_common.cuh"
 
@@ -125,7 +127,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   float *red4 = Et + 128;                                             // [4]
   int32_t *s_rule = reinterpret_cast<int32_t *>(misc + 36);           // firing rule of the claimed tile
   long long *s_prefix = reinterpret_cast<long long *>(misc + 40);
-  uint32_t *s_red = reinterpret_cast<uint32_t *>(misc + 1664);       // [2][4] warps' largest |x| per pass
+  uint32_t *s_red = reinterpret_cast<uint32_t *>(misc + 1664);       // [3][4] warps' maxima
   uint32_t *tmem_slot0 = reinterpret_cast<uint32_t *>(pipe0 + 2 * (kTGroups + S) * 1024 + 32);
 
   const int tid = cta_tid % kTPipeThreads, warp = tid >> 5, lane = cta_tid & 31;  // within the pipeline
@@ -262,44 +264,73 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     };
     if (f.hist_out && k == f.frames - 1 && s0 + nv == f.L)
       for (int i = tid; i < f.T - 1; i += kTPipeThreads) f.hist_out[i] = cur[f.L - (f.T - 1) + i];
-    int sx = sx_pred;
-    for (int pass = 0;; ++pass) {
-      const float xsc = exp2i(sx);
-      float mx = 0.f;
-      for (int q0 = 0; q0 < npieces; q0 += kTMaxPieces * kTPipeThreads) {
-        float v[kTMaxPieces][8];
+    // the tile scaled by 2^sx, sx predicted from the pipeline's previous
+    // tile (no multiply when it is 0); the largest FP16 hi part gives the
+    // tile's own exponent after the barrier that ends the conversion, and a
+    // tile whose own exponent differs is converted once more (uniform,
+    // rare): the exponent a tile is fired with depends on the tile alone
+    // loads in flight per thread: fewer with four pipelines (128 registers)
+    constexpr int kPieces = NP == 4 ? 3 : kTMaxPieces;
+    auto convert = [&](int sxc) -> uint32_t {
+      const float xsc = exp2i(sxc);
+      uint32_t hm = 0u;
+      for (int q0 = 0; q0 < npieces; q0 += kPieces * kTPipeThreads) {
+        float v[kPieces][8];
 #pragma unroll
-        for (int i = 0; i < kTMaxPieces; ++i) {
+        for (int i = 0; i < kPieces; ++i) {
           const int q = q0 + tid + kTPipeThreads * i;
           if (q < npieces) load_piece(q, v[i]);
         }
 #pragma unroll
-        for (int i = 0; i < kTMaxPieces; ++i) {
+        for (int i = 0; i < kPieces; ++i) {
           const int q = q0 + tid + kTPipeThreads * i;
           if (q >= npieces) continue;
+          // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            mx = fmaxf(mx, fabsf(v[i][e]));
-            if (sx != 0) v[i][e] *= xsc;
-          }
+          for (int e = 0; e < 8; ++e) v[i][e] *= xsc;
           const int row = q >> 3, pc = q & 7;
           const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-          *reinterpret_cast<uint4 *>(ahi + off) = split_pack8(v[i], false);
-          *reinterpret_cast<uint4 *>(alo + off) = split_pack8(v[i], true);
+          uint4 h4, l4;
+          split_pair(v[i][0], v[i][1], h4.x, l4.x);
+          split_pair(v[i][2], v[i][3], h4.y, l4.y);
+          split_pair(v[i][4], v[i][5], h4.z, l4.z);
+          split_pair(v[i][6], v[i][7], h4.w, l4.w);
+          hmax_abs_acc(hm, h4.x);
+          hmax_abs_acc(hm, h4.y);
+          hmax_abs_acc(hm, h4.z);
+          hmax_abs_acc(hm, h4.w);
+          *reinterpret_cast<uint4 *>(ahi + off) = h4;
+          *reinterpret_cast<uint4 *>(alo + off) = l4;
         }
       }
-      // the tile's largest component, exchanged through the barrier that
-      // ends the conversion (a buffer per pass); a tile the predicted scale
-      // does not fit is converted once more with its own (uniform)
-      uint32_t *cr = s_red + 4 * pass;
-      const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-      if (lane == 0) cr[warp] = wm;
+      return hm;
+    };
+    int sx = sx_pred;
+    for (int pass = 0;; ++pass) {
+      const uint32_t hm = convert(sx);
+      // s_red: [hi max of pass 0, of pass 1, FP32 max][4 warps]
+      const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax_abs_bits(hm));
+      if (lane == 0) s_red[4 * pass + warp] = wm;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
       psync();
-      const uint32_t tm = max(max(cr[0], cr[1]), max(cr[2], cr[3]));
-      if (pass == 1 || tc_shift_fits(tm, sx)) break;
-      sx = tc_shift_bits(tm);
+      if (pass == 1) break;
+      int own = tc_shift_from_hi(max(max(s_red[0], s_red[1]), max(s_red[2], s_red[3])), sx);
+      if (own == -1000) {  // zero, subnormal or inf hi parts: the FP32 maximum decides
+        float mx = 0.f;
+        for (int q = tid; q < npieces; q += kTPipeThreads) {
+          float v[8];
+          load_piece(q, v);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(v[e]));
+        }
+        const uint32_t fm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if (lane == 0) s_red[8 + warp] = fm;
+        psync();
+        own = tc_shift_bits(max(max(s_red[8], s_red[9]), max(s_red[10], s_red[11])));
+      }
+      if (own == sx) break;
+      sx = own;
     }
     sx_pred = sx;
 

@@ -33,6 +33,8 @@
 // memory is freed, each thread that issued GEMMs commits once more to a
 // barrier of its own and waits for it (all its GEMMs have completed).
 #pragma once
+#include <type_traits>
+
 #include "firing_loop_tc.cuh"
 
 namespace prune {
@@ -70,6 +72,15 @@ struct WsGroup {
   int32_t pad;
   long long prefix;
 };
+
+// The misc region: mbarriers [0, 256), item records [256, 448), the TMEM
+// slot and stop flag [512, 520), the converter's maxima [528, 624), the
+// epilogue groups' scratch from 1024.
+constexpr uint32_t kWsGroupOff = 1024;
+static_assert(kWsGroupOff + kWsGroups * sizeof(WsGroup) <= kWsMiscBytes, "the groups' scratch fits the misc region");
+static_assert(24 * sizeof(uint64_t) <= 256, "the mbarriers fit [0, 256)");
+static_assert(528 + 24 * sizeof(uint32_t) <= kWsGroupOff, "the converter's maxima fit [528, 1024)");
+static_assert(8 * sizeof(WsItem) <= 192, "the item records fit [256, 448)");
 
 // Cold paths.  They stay inlined: as calls, the register saves around them
 // cost the hot loops more than their code does.
@@ -127,8 +138,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   WsItem *item_slot = item_a + 2;                                   // [4]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 512);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 520);
-  WsGroup *grp = reinterpret_cast<WsGroup *>(misc + 1024);          // [3]
-  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 4096);       // [4] converter warps' largest |x|
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 528);         // [2][3][4] converter warps' maxima
+  WsGroup *grp = reinterpret_cast<WsGroup *>(misc + kWsGroupOff);   // [3]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
   const unsigned long long kSentinel = ~0ull;
@@ -168,7 +179,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     uint32_t i = 0;            // items armed so far (a failed wait leaves before arming item i)
     for (; sentinels < kWsGroups; ++i) {
       const int s = i & 1;
-      if (i >= 2 && !ws_wait(smem_u32(&raw_empty[s]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop)) {
+      if (i >= 2 && !__all_sync(0xffffffffu, ws_wait(smem_u32(&raw_empty[s]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop))) {
         if (lane == 0) fail(kActFir, 10, 0);
         break;
       }
@@ -250,11 +261,12 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     bool issued = false;
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
       const int b = i & 1, j = i & 3;
-      if (!ws_wait(smem_u32(&a_full[b]), (i >> 1) & 1u, p.timeout_ns, stop)) {
+      if (!__all_sync(0xffffffffu, ws_wait(smem_u32(&a_full[b]), (i >> 1) & 1u, p.timeout_ns, stop))) {
         if (lane == 0) fail(kActFir, 11, 0);
         break;
       }
-      if (i >= kWsSlots && !ws_wait(smem_u32(&slot_empty[j]), ((i >> 2) - 1) & 1u, p.timeout_ns, stop)) {
+      if (i >= kWsSlots &&
+          !__all_sync(0xffffffffu, ws_wait(smem_u32(&slot_empty[j]), ((i >> 2) - 1) & 1u, p.timeout_ns, stop))) {
         if (lane == 0) fail(kActFir, 12, 0);
         break;
       }
@@ -301,94 +313,115 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     int sx_pred = 0;          // scale exponent of this converter's previous tile
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
       const int s = i & 1, b = i & 1;
-      if (!ws_wait(smem_u32(&raw_full[s]), (i >> 1) & 1u, p.timeout_ns, stop)) {
-        if (ct == 0) fail(kActFir, 13, 0);
-        break;
-      }
-      if (i >= 2 && !ws_wait(smem_u32(&a_empty[b]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop)) {
-        if (ct == 0) fail(kActFir, 14, 0);
-        break;
-      }
+      // every converter thread waits (it reads what the copies wrote); the
+      // outcomes are combined at the barrier that ends the conversion, which
+      // the tile path and the sentinel path both reach once (a thread whose
+      // wait gave up converts nothing), so the warpgroup leaves together
+      const bool okr = ws_wait(smem_u32(&raw_full[s]), (i >> 1) & 1u, p.timeout_ns, stop);
+      const bool oka = !okr || i < 2 || ws_wait(smem_u32(&a_empty[b]), ((i >> 1) - 1) & 1u, p.timeout_ns, stop);
+      const bool okw = okr && oka;
       WsItem it = item_raw[s];
-      if (it.t != kSentinel) {
-        const unsigned char *raw = raw0 + s * kWsRawBytes;
-        unsigned char *ahi = aop0 + b * kWsAOpBytes;
-        unsigned char *alo = ahi + (kTGroups + S) * 1024;
-        const int npieces = (kTGroups + S) * 64;
-        // kWsConvBatch pieces per thread at a time: all their loads are
-        // issued before the first split, so the load latency is paid once
-        // per batch.  The pieces are scaled by 2^sx (no multiply for 2^0),
-        // sx predicted from the converter's previous tile; the tile's
-        // largest component, gathered on the way, is exchanged through the
-        // barrier that ends the conversion, and a tile whose prediction does
-        // not fit is converted once more with its own sx (uniform).
-        int sx = sx_pred;
-        for (int pass = 0;; ++pass) {
-          const float xsc = exp2i(sx);
-          float mx = 0.f;
-          for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
-            float4 u[kWsConvBatch][2];
+      const unsigned char *raw = raw0 + s * kWsRawBytes;
+      unsigned char *ahi = aop0 + b * kWsAOpBytes;
+      unsigned char *alo = ahi + (kTGroups + S) * 1024;
+      const int npieces = (kTGroups + S) * 64;
+      // cred: [item parity][hi max, FP32 max, spare][4 warps]: no thread
+      // rewrites a buffer that another may still read
+      uint32_t *cr = cred + (i & 1u) * 12u;
+      // kWsConvBatch pieces per thread at a time: all their loads are
+      // issued before the first split, so the load latency is paid once per
+      // batch.  The pieces are scaled by 2^sx (a multiply by 1 for 2^0: one
+      // instantiation keeps the converter's code small, which measured
+      // faster than a second, multiply-free copy); the largest FP16 hi part
+      // is gathered on the way (one packed max per two components).
+      auto convert = [&](int sxc) -> uint32_t {
+        const float xsc = exp2i(sxc);
+        uint32_t hm = 0u;
+        for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
+          float4 u[kWsConvBatch][2];
 #pragma unroll
-            for (int r = 0; r < kWsConvBatch; ++r) {
-              const int q = q0 + 128 * r;
-              const int row = q >> 3, pc = q & 7;
-              const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
-              if (q < npieces && kTR * j + 4 * pc < it.nv) {
-                // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read
-                // their halves in the other order, so each quarter-warp load
-                // covers all 32 banks once
-                const float4 *src =
-                    reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
-                const int sw = (pc >> 2) & 1;
-                const float4 a0 = src[sw], a1 = src[sw ^ 1];
-                u[r][0] = sw ? a1 : a0;
-                u[r][1] = sw ? a0 : a1;
-              } else {
-                u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                u[r][1] = u[r][0];
-              }
-            }
-#pragma unroll
-            for (int r = 0; r < kWsConvBatch; ++r) {
-              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[r][0].x), fabsf(u[r][0].y)), fmaxf(fabsf(u[r][0].z), fabsf(u[r][0].w))));
-              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(u[r][1].x), fabsf(u[r][1].y)), fmaxf(fabsf(u[r][1].z), fabsf(u[r][1].w))));
-              if (sx != 0) {
-                u[r][0].x *= xsc; u[r][0].y *= xsc; u[r][0].z *= xsc; u[r][0].w *= xsc;
-                u[r][1].x *= xsc; u[r][1].y *= xsc; u[r][1].z *= xsc; u[r][1].w *= xsc;
-              }
-            }
-#pragma unroll
-            for (int r = 0; r < kWsConvBatch; ++r) {
-              const int q = q0 + 128 * r;
-              if (q < npieces) {
-                const int row = q >> 3, pc = q & 7;
-                const uint32_t off =
-                    static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-                uint4 h4, l4;
-                split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
-                split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
-                split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
-                split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
-                *reinterpret_cast<uint4 *>(ahi + off) = h4;
-                *reinterpret_cast<uint4 *>(alo + off) = l4;
-              }
+          for (int r = 0; r < kWsConvBatch; ++r) {
+            const int q = q0 + 128 * r;
+            const int row = q >> 3, pc = q & 7;
+            const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
+            if (q < npieces && kTR * j + 4 * pc < it.nv) {
+              // the 8 pieces of a row are 32 bytes apart: pieces 4-7 read
+              // their halves in the other order, so each quarter-warp load
+              // covers all 32 banks once
+              const float4 *src = reinterpret_cast<const float4 *>(raw + (kWsRawHalo + kTR * j + 4 * pc) * 8);
+              const int sw = (pc >> 2) & 1;
+              const float4 a0 = src[sw], a1 = src[sw ^ 1];
+              u[r][0] = sw ? a1 : a0;
+              u[r][1] = sw ? a0 : a1;
+            } else {
+              u[r][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+              u[r][1] = u[r][0];
             }
           }
-          // cred has a buffer per (item parity, pass): no thread rewrites one
-          // that another may still read
-          uint32_t *cr = cred + ((i & 1u) * 2u + static_cast<uint32_t>(pass)) * 4u;
-          const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-          if (lane == 0) cr[warp - 2] = wm;
+#pragma unroll
+          for (int r = 0; r < kWsConvBatch; ++r) {
+            const int q = q0 + 128 * r;
+            if (q < npieces) {
+              u[r][0].x *= xsc; u[r][0].y *= xsc; u[r][0].z *= xsc; u[r][0].w *= xsc;
+              u[r][1].x *= xsc; u[r][1].y *= xsc; u[r][1].z *= xsc; u[r][1].w *= xsc;
+              const int row = q >> 3, pc = q & 7;
+              const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
+              uint4 h4, l4;
+              split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
+              split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
+              split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
+              split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
+              hmax_abs_acc(hm, h4.x);
+              hmax_abs_acc(hm, h4.y);
+              hmax_abs_acc(hm, h4.z);
+              hmax_abs_acc(hm, h4.w);
+              *reinterpret_cast<uint4 *>(ahi + off) = h4;
+              *reinterpret_cast<uint4 *>(alo + off) = l4;
+            }
+          }
+        }
+        return hm;
+      };
+      // the tile split with the exponent predicted from the converter's
+      // previous tile
+      int sx = sx_pred;
+      if (okw && it.t != kSentinel) {
+        const uint32_t hm = convert(sx);
+        const uint32_t wm = __reduce_max_sync(0xffffffffu, hmax_abs_bits(hm));
+        if (lane == 0) cr[warp - 2] = wm;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      if (!bar_and(1, 128, okw)) {
+        if (ct == 0) fail(kActFir, okr ? 14 : 13, 0);
+        break;
+      }
+      if (it.t != kSentinel) {
+        // the tile's own exponent from its largest hi part; a tile whose
+        // own exponent differs from the prediction is converted once more
+        // (uniform, rare): the exponent a tile is fired with depends on the
+        // tile alone, never on the prediction
+        int own = tc_shift_from_hi(max(max(cr[0], cr[1]), max(cr[2], cr[3])), sx);
+        if (own == -1000) {  // zero, subnormal or inf hi parts: the FP32 maximum decides
+          const int halo = S * kTR;
+          const float4 *w4 = reinterpret_cast<const float4 *>(raw + (kWsRawHalo - halo) * 8);
+          float mx = 0.f;
+          for (int q = ct; q < (halo + it.nv) / 2; q += 128) {
+            const float4 a = w4[q];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+          }
+          const uint32_t fm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+          if (lane == 0) cr[4 + warp - 2] = fm;
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          own = tc_shift_bits(max(max(cr[4], cr[5]), max(cr[6], cr[7])));
+        }
+        if (own != sx) {
+          sx = own;
+          convert(sx);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("bar.sync 1, 128;" ::: "memory");
-          const uint32_t tm = max(max(cr[0], cr[1]), max(cr[2], cr[3]));
-          if (pass == 1 || tc_shift_fits(tm, sx)) break;
-          sx = tc_shift_bits(tm);
         }
         it.sx = sx;
         sx_pred = sx;
-      } else {
-        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
       if (ct == 0) {
         item_a[b] = it;
@@ -415,12 +448,11 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     for (uint32_t i = static_cast<uint32_t>(e);; i += kWsGroups) {
       const int j = i & 3;
       const uint32_t use = i >> 2;
-      if (!ws_wait(smem_u32(&fir_full[j]), use & 1u, p.timeout_ns, stop)) {
-        if (gt == 0) fail(kActFir, 15, 0);
-        break;
-      }
+      // every thread waits; the outcomes are combined at the barrier that
+      // ends the read-back (a thread whose wait gave up touches no tensor
+      // memory and its record is not used), so the group leaves together
+      const bool okf = ws_wait(smem_u32(&fir_full[j]), use & 1u, p.timeout_ns, stop);
       const WsItem it = item_slot[j];
-      if (it.t == kSentinel) break;
       tc_fence_after();
       const int k = it.k, tile = it.tile, nv = it.nv;
       const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
@@ -431,7 +463,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       //      energies; each 16-column quarter, times 2^m, split into the HX
       //      operand over the columns 64 + 16 qd .. + 15 it came from (hi in
       //      the first 8, lo in the next 8, two FP16 per column)
-      {
+      if (okf && it.t != kSentinel) {
         const float hsc = exp2i(tp.m);
         float en = 0.f;
 #pragma unroll 1
@@ -455,7 +487,11 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         tmem_st_wait();
       }
       tc_fence_before();
-      gsync();
+      if (!bar_and(static_cast<uint32_t>(bar), 128, okf)) {
+        if (gt == 0) fail(kActFir, 15, 0);
+        break;
+      }
+      if (it.t == kSentinel) break;
       // ---- HX_b GEMM on all 128 rows with its A operand in tensor memory,
       //      issued by the group's last warp while the first runs the block
       //      energies, SEL and the look-back (rows of unselected blocks are
@@ -524,13 +560,11 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       }
       const int64_t rs = p.rslot.slot(k);
       if (gt < nb && G.rank[gt] >= 0) p.rec_idx[rs * f.F + prefix + G.rank[gt]] = static_cast<int32_t>(s0 / f.B) + gt;
-      // ---- SINK payload: the selected rows at their compacted places
-      if (!ws_wait(smem_u32(&hx_full[j]), use & 1u, p.timeout_ns, stop)) {
-        if (gt == 0) fail(kActHx, 7, seq);
-        break;
-      }
+      // ---- SINK payload: the selected rows at their compacted places (the
+      //      wait outcomes are combined at the completion barrier below)
+      const bool okh = ws_wait(smem_u32(&hx_full[j]), use & 1u, p.timeout_ns, stop);
       tc_fence_after();
-      if (cnt > 0) {
+      if (okh && cnt > 0) {
         const int rk = jc < rows_valid ? G.rank[jc / rpb] : -1;
         float f1, f2;  // HX outputs are H y 2^(sx + s_taps + m + s_h)
         pow2_pair(-(it.sx + tp.s_taps + tp.m + tp.s_h), f1, f2);
@@ -553,7 +587,10 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       }
       // ---- frame completion; the slot goes back to the MMA warp
       tc_fence_before();
-      gsync();
+      if (!bar_and(static_cast<uint32_t>(bar), 128, okh)) {
+        if (gt == 0) fail(kActHx, 7, seq);
+        break;
+      }
       if (gw == 0) {
         int last = 0;
         if (lane == 0) {

@@ -80,6 +80,19 @@ __host__ inline cudaError_t tc_prepare_ops(const float2 *taps, int T, const floa
   return cudaGetLastError();
 }
 
+// A named barrier over nthreads threads that also ANDs a predicate across
+// them: the outcome of per-thread bounded waits becomes the group's, so no
+// thread leaves a loop whose next named barrier the others still reach.
+__device__ __forceinline__ bool bar_and(uint32_t id, uint32_t nthreads, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n barrier.cta.red.and.pred b, %2, %3, a;\n selp.u32 %0, 1, 0, b;\n}"
+      : "=r"(r)
+      : "r"(p ? 1u : 0u), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
 // Bounded mbarrier wait that also gives up when the CTA's stop flag is set.
 __device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, uint64_t timeout_ns,
                                         const volatile int32_t *stop) {

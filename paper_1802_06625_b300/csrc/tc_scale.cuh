@@ -6,9 +6,12 @@
 // normal (components far below M, whose lo parts are subnormal, carry an
 // absolute error of at most 2^-25, below 2^-21 M / 16).  So an operand whose
 // M is in that window is used as it is (scale 2^0, no multiply), and any
-// other is scaled by 2^s so that M 2^s lies in [2^14, 2^15).  Results are
-// scaled back by 2^-s; a scaling by 2^n changes no rounding as long as the
-// values stay normal floats.
+// other is scaled by 2^s, s a multiple of 8, so that M 2^s lies in
+// [2^7, 2^15).  The exponent s is a function of M's exponent alone (so a
+// tile gets the same scale whichever CTA fires it, and results do not depend
+// on scheduling), and its steps of 8 let consecutive tiles of a signal share
+// it.  Results are scaled back by 2^-s; a scaling by 2^n changes no
+// rounding as long as the values stay normal floats.
 //
 // The constant operands (taps, H) are scaled once per graph on the host;
 // their exponents travel in the kernels' parameter records.
@@ -21,29 +24,43 @@
 
 namespace prune {
 
-constexpr int kTTop = 14;                // scaled operands: largest component in [2^14, 2^15)
-constexpr int kTMaxUp = 100;             // largest up-scaling (a tile whose largest |x| < 2^-86)
+constexpr int kTTop = 14;                // the window: largest component in [2^0, 2^(kTTop+1))
+constexpr int kTMaxUp = 96;              // largest up-scaling (a tile whose largest |x| < 2^-89 keeps it)
 
-// Exponent s for a largest magnitude with float bits `b` (sign ignored):
-// 0 inside the window [2^0, 2^15) and for zero, inf and NaN; otherwise the s
-// that brings it into [2^14, 2^15), at most kTMaxUp.
-__host__ __device__ __forceinline__ int tc_shift_bits(uint32_t b) {
-  const int e = static_cast<int>((b >> 23) & 0xFFu);
-  if (e == 255 || (b & 0x7FFFFFFFu) == 0u) return 0;
+// Exponent s for a largest magnitude M, given its biased float exponent e
+// (255 for inf / NaN; e of zero = 0 with M = 0): 0 inside the window and for
+// zero, inf and NaN; otherwise the multiple of 8 with e + s in [134, 141],
+// at most kTMaxUp.
+__host__ __device__ __forceinline__ int tc_shift_exp(int e, bool zero) {
+  if (e >= 255 || zero) return 0;
   if (e >= 127 && e <= 127 + kTTop) return 0;
-  const int s = 127 + kTTop - (e > 1 ? e : 1);
+  const int d = 127 + kTTop - (e > 1 ? e : 1);       // > 14 or < 0
+  const int s = d >= 0 ? (d / 8) * 8 : -(((-d) + 7) / 8) * 8;
   return s < kTMaxUp ? s : kTMaxUp;
+}
+__host__ __device__ __forceinline__ int tc_shift_bits(uint32_t b) {
+  return tc_shift_exp(static_cast<int>((b >> 23) & 0xFFu), (b & 0x7FFFFFFFu) == 0u);
 }
 __device__ __forceinline__ int tc_pow2_shift(float mx) { return tc_shift_bits(__float_as_uint(mx)); }
 
-// Does the largest magnitude M (bits b), scaled by 2^s, fit the window
-// [2^0, 2^15)?  (Zero, inf and NaN fit any s: zeros stay zero, non-finite
-// values propagate whatever the scale.)
-__device__ __forceinline__ bool tc_shift_fits(uint32_t b, int s) {
-  const int e = static_cast<int>((b >> 23) & 0xFFu);
-  if (e == 255 || (b & 0x7FFFFFFFu) == 0u) return true;
-  const int es = e + s;  // exponent field of M 2^s (M normal; a subnormal M fails below)
-  return e >= 1 && es >= 127 && es <= 127 + kTTop;
+// The largest |component| of FP16 hi parts, kept as a packed pair whose
+// signs are meaningless (max.xorsign.abs: |result| = max(|a|, |b|); NaN
+// operands are skipped).
+__device__ __forceinline__ void hmax_abs_acc(uint32_t &acc, uint32_t h2) {
+  asm("max.xorsign.abs.f16x2 %0, %0, %1;" : "+r"(acc) : "r"(h2));
+}
+__device__ __forceinline__ uint32_t hmax_abs_bits(uint32_t acc) {  // FP16 bits of the larger magnitude
+  return max(acc & 0x7FFFu, (acc >> 16) & 0x7FFFu);
+}
+// Given the FP16 bits h of the largest hi part of a tile converted with the
+// predicted exponent s (hi = the component scaled by 2^s with its low 13
+// mantissa bits cleared, so its FP16 exponent is that of the scaled
+// component when it is a normal FP16): the tile's own exponent, or -1000 when
+// h cannot tell (zero, subnormal, inf: the caller finds the FP32 maximum).
+__device__ __forceinline__ int tc_shift_from_hi(uint32_t h, int s) {
+  if (h < 0x0400u || h >= 0x7C00u) return -1000;
+  const int e = static_cast<int>(h >> 10) - 15 + 127 - s;       // biased FP32 exponent of M
+  return tc_shift_exp(e, false);
 }
 
 // 2^n as a float for n in [-149, 127] (subnormal below -126); clamped.

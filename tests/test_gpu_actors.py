@@ -100,6 +100,25 @@ def test_det_sel_extremes(G):
     assert list(c.cpu().numpy()) == [2, 1] and list(idx.cpu().numpy()[0, :2]) == [2, 3]
 
 
+def _oracle_hx(y, sel, H, F, B, N):
+    """HX_b of the oracle on the given blocks: frames y [frames, F, B] fired
+    through the oracle's graph with one unit tap (the FIR is the identity,
+    T = 1) and tau between the energies of the chosen blocks and of the
+    others (the others are scaled down by 1e-3 beforehand), so DET selects
+    exactly `sel[k]`.  Returns the oracle's compacted outputs per frame."""
+    frames = y.shape[0]
+    x = y.copy()
+    for k in range(frames):
+        mask = np.ones(F, bool)
+        mask[sel[k]] = False
+        x[k, mask] *= np.float32(1e-3)
+    tau = np.float32(1e-3 * B)       # selected blocks: E ~ B, the others: E ~ 1e-6 B
+    r = oracle.run(F, B, 1, N, tau, np.ones(1, np.complex64), H, x.astype(np.complex64))
+    for k in range(frames):
+        assert np.array_equal(np.asarray(r.idx[k]), sel[k])
+    return x, r
+
+
 @pytest.mark.parametrize("N,B", [(1, 64), (2, 64), (4, 256), (8, 256), (16, 256), (32, 1024), (12, 96 * 8), (24, 768),
                                  (64, 64), (64, 256), (64, 512), (64, 2048)])
 def test_hx_matches_oracle(G, N, B):
@@ -108,15 +127,15 @@ def test_hx_matches_oracle(G, N, B):
     y = _rc(rng, frames, F, B)
     H = _rc(rng, N, N, scale=1 / np.sqrt(N))
     sel = [np.sort(rng.choice(F, size=s, replace=False)) for s in (4, 0)]
+    x, r = _oracle_hx(y, sel, H, F, B, N)
     c = np.array([len(s) for s in sel], np.int32)
     idx = np.full((frames, F), 0, np.int32)
     for k, s in enumerate(sel):
         idx[k, :len(s)] = s
-    out = G.hx(torch.from_numpy(y.reshape(frames, -1)).cuda(), torch.from_numpy(idx).cuda(),
+    out = G.hx(torch.from_numpy(x.reshape(frames, -1)).cuda(), torch.from_numpy(idx).cuda(),
                torch.from_numpy(c).cuda(), torch.from_numpy(H), F, B, N).cpu().numpy().reshape(frames, F, B)
     for k in range(frames):
-        X = y[k, sel[k]].reshape(len(sel[k]), B // N, N).astype(np.complex128)
-        want = np.einsum("ik,bjk->bji", H.astype(np.complex128), X).reshape(len(sel[k]), B)
+        want = np.asarray(r.y[k])
         got = out[k, :c[k]]
         if c[k]:
             rms = np.sqrt(np.mean(np.abs(want) ** 2))
@@ -146,21 +165,21 @@ def test_hx_cyclic_shift_is_a_permutation(G, N):
 
 def test_hx_tensor_core_many_tiles_and_frames(G):
     """N = 64 on tcgen05 with uneven c per frame: several 128-row tiles, a
-    ragged last tile, c = 0 and c = F frames."""
+    ragged last tile, c = 0 and c = F frames, against the oracle."""
     rng = np.random.default_rng(99)
     N, B, F, frames = 64, 256, 70, 4
     y = _rc(rng, frames, F, B, scale=4.0)
     H = _rc(rng, N, N, scale=1 / np.sqrt(N))
     sel = [np.sort(rng.choice(F, size=s, replace=False)) for s in (33, 0, F, 1)]
+    x, r = _oracle_hx(y, sel, H, F, B, N)
     c = np.array([len(s) for s in sel], np.int32)
     idx = np.zeros((frames, F), np.int32)
     for k, s_ in enumerate(sel):
         idx[k, :len(s_)] = s_
-    out = G.hx(torch.from_numpy(y.reshape(frames, -1)).cuda(), torch.from_numpy(idx).cuda(),
+    out = G.hx(torch.from_numpy(x.reshape(frames, -1)).cuda(), torch.from_numpy(idx).cuda(),
                torch.from_numpy(c).cuda(), torch.from_numpy(H), F, B, N).cpu().numpy().reshape(frames, F, B)
     for k in range(frames):
-        X = y[k, sel[k]].reshape(len(sel[k]), B // N, N).astype(np.complex128)
-        want = np.einsum("ik,bjk->bji", H.astype(np.complex128), X).reshape(len(sel[k]), B)
+        want = np.asarray(r.y[k])
         if c[k]:
             rms = np.sqrt(np.mean(np.abs(want) ** 2))
             assert np.max(np.abs(out[k, :c[k]] - want)) <= TOL_REL * rms

@@ -18,7 +18,7 @@ def test_bench_line_contract():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     cmd = [sys.executable, "bench.py", "--steps", "1", "--warmup", "3", "--frames", "48", "--C", "48",
-           "--no-batched", "--no-serving", "--no-dpd", "--e2e-frames", "3", "--cpu-frames", "1"]
+           "--no-batched", "--no-serving", "--no-dpd", "--no-small", "--no-diff", "--e2e-frames", "3", "--cpu-frames", "1"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]

@@ -4,9 +4,10 @@ bench times, against the oracle.
 - Plain large (1000 frames of 4096 blocks x 1024 samples, T = 64, N = 32):
   fired exactly as the bench fires it (frames resident on the device, pushed
   by reference in runs of C = 336, the warp-specialised tensor-core loop).
-  The oracle fires every frame on the host, in frame ranges spread over
-  spawned worker processes (each range is fed the tail of the frame before
-  it as its delay token).  c and idx of all 1000 frames are compared
+  The oracle fires every frame on the host cores, frame by frame in spawned
+  worker processes (each frame is fed the tail of the frame before it as
+  its delay token; the frames are drawn again by the seeded generator and
+  sent with the tasks).  c and idx of all 1000 frames are compared
   bit-exactly outside the guard band; the samples are checked on sampled
   frames elsewhere.
 - Batched (one step of the 512 uneven instances, N = 64, tensor-core FIR
@@ -32,8 +33,25 @@ import oracle_ranges
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-def _workers():
-    return max(1, min(32, os.cpu_count() or 1))
+def _pool():
+    nw = max(1, min(16, (os.cpu_count() or 2) - 1))
+    return mp.get_context("spawn").Pool(nw)
+
+
+def _ordered(pool, fn, tasks, n, per_result_s=300):
+    """Results of fn over the tasks, in order; a result that takes longer
+    than per_result_s (a lost worker) fails the test instead of waiting."""
+    it = pool.imap(fn, tasks, chunksize=1)
+    out = []
+    try:
+        for _ in range(n):
+            out.append(it.next(timeout=per_result_s))
+    except mp.TimeoutError:
+        pool.terminate()
+        raise
+    pool.close()
+    pool.join()
+    return out
 
 
 def _check_control(c_g, idx_g, c_o, idx_o, energy_o, tau, F):
@@ -60,14 +78,6 @@ def test_plain_large_every_frame_control_against_oracle():
 
     w = synth.PLAIN_LARGE
     n, C = w.frames, 336
-    # the oracle's frame ranges start first, in spawned processes, and run
-    # while the GPU fires the stream
-    nw = _workers()
-    bounds = np.linspace(0, n, 4 * nw + 1).astype(int)
-    ctx = mp.get_context("spawn")
-    pool = ctx.Pool(nw)
-    pending = pool.map_async(oracle_ranges.plain_range, list(zip(bounds[:-1], bounds[1:])))
-
     dev = torch.device("cuda", 0)
     x = torch.empty(n, w.F, w.B, dtype=torch.complex64, device=dev)
     for k in range(n):
@@ -102,12 +112,21 @@ def test_plain_large_every_frame_control_against_oracle():
             done += q
     g.close()
     del x, y_d
+    torch.cuda.empty_cache()
 
-    results = [r for part in pending.get(timeout=3600) for r in part]
-    pool.close()
-    pool.join()
-    assert [r[0] for r in results] == list(range(n))
-    tau = np.float32(w.tau)
+    # the oracle fires every frame on the host cores; the frames are drawn
+    # again by the seeded generator and sent with each task, each fed the
+    # tail of the frame before it as its delay token
+    taps, H, tau = w.taps().numpy(), w.H().numpy(), np.float32(w.tau)
+
+    def tasks():
+        prev = None
+        for k in range(n):
+            xk = w.frame(k, device=dev).cpu().numpy()
+            yield (k, w.F, w.B, w.T, w.N, tau, taps, H, xk, prev)
+            prev = xk.reshape(-1)[-(w.T - 1):].copy()
+
+    results = _ordered(_pool(), oracle_ranges.fire_frame, tasks(), n)
     band = 0
     for k, c_o, idx_o, e_o in results:
         band += _check_control(int(got_c[k]), got_idx[k], c_o, idx_o, e_o, tau, w.F)
@@ -121,26 +140,23 @@ def test_batched_every_instance_against_oracle():
     from paper_1802_06625_b300.graph import Batch
 
     b = synth.BATCHED
-    nw = _workers()
-    ids = list(range(b.instances))
-    parts = [ids[i::4 * nw] for i in range(4 * nw)]
-    ctx = mp.get_context("spawn")
-    pool = ctx.Pool(nw)
-    pending = pool.map_async(oracle_ranges.batched_instances, parts)
-
-    ws = [b.instance(i) for i in ids]
+    ws = [b.instance(i) for i in range(b.instances)]
     dev = torch.device("cuda", 0)
     x = torch.cat([w.frame(0, device=dev).reshape(-1) for w in ws])
     bt = Batch(b.B, b.N, [{"F": w.F, "T": w.T, "tau": w.tau, "taps": w.taps(), "H": w.H()} for w in ws], device=0)
     bt.autotune(x, reps=1)
     bt.fire(x, graph=True)
     bt.sync()
-    got = [bt.pull(i) for i in ids]
+    got = [bt.pull(i) for i in range(b.instances)]
     bt.close()
+    del x
 
-    results = {r[0]: r[1:] for part in pending.get(timeout=3600) for r in part}
-    pool.close()
-    pool.join()
+    def tasks():
+        for i, w in enumerate(ws):
+            yield (i, w.F, w.B, w.T, w.N, np.float32(w.tau), w.taps().numpy(), w.H().numpy(),
+                   w.frame(0, device=dev).cpu().numpy())
+
+    results = {r[0]: r[1:] for r in _ordered(_pool(), oracle_ranges.fire_instance, tasks(), b.instances)}
     band_by_T = {}
     worst = 0.0
     for i, w in enumerate(ws):

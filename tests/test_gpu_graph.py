@@ -96,7 +96,10 @@ def test_ragged_and_degenerate_shapes(G, F, B, T, N, C, frames):
                                               (9, 512, 128, 32, 2, 3), (3, 2048, 1, 32, 3, 4),
                                               (130, 32, 33, 32, 3, 3), (37, 128, 17, 32, 4, 6),
                                               (7, 1024, 129, 32, 1, 3), (300, 256, 64, 32, 3, 3),
-                                              (70, 64, 48, 32, 3, 3)])
+                                              (70, 64, 48, 32, 3, 3),
+                                              # T = 65 is the warp-specialised loop's last T (3 shifts),
+                                              # T = 66 the tile-pipeline loop's first (4 shifts)
+                                              (24, 1024, 65, 32, 3, 4), (24, 1024, 66, 32, 3, 4)])
 @pytest.mark.parametrize("path", PATHS)
 def test_tensor_core_loop_shapes(G, F, B, T, N, C, frames, path):
     w = synth.PlainWorkload("t", F=F, B=B, T=T, N=N, frames=frames, tau=4.0 * B, seed=F * 7 + B + T, p=0.45, C=C)
