@@ -302,9 +302,10 @@ def run_ours(args, w):
             if kind == 6:   # tensor pipe: split-FP16 FIR (ns shifts) + HX
                 ns = 1 + (w.T - 1 + 31) // 32
                 if ws_loop:
-                    # per 128-row tile: ns x 4 K steps x 2 GEMMs of 128 x 128 x 16 (FIR), 3 passes x 4
-                    # K steps of 128 x 64 x 16 (HX on all rows): per sample ns * 1024 + 768 flop
-                    per_sample, note = ns * 1024.0 + 768.0, "FIR as 2 N=128 GEMMs per K step (hi and lo data), HX 3 passes on all rows"
+                    # per 128-row tile: ns x 4 K steps x (128 x 128 x 16 + 128 x 64 x 16) (FIR), 3 passes
+                    # x 4 K steps of 128 x 64 x 16 (HX on all rows): per sample (ns + 1) * 768 flop
+                    per_sample, note = (ns + 1) * 768.0, ("FIR per K step as hi x [taps hi | lo] (N=128) and lo x taps hi "
+                                                          "(N=64), HX 3 passes on all rows")
                 else:
                     # 3 passes x 4 K steps of 128 x 64 x 16 per shift (FIR), HX on the selected rows
                     per_sample, note = (ns + sel_frac) * 768.0, "FIR and HX in 3 split passes, HX on the selected rows"
@@ -874,7 +875,7 @@ def run_e2e(args, w, dev, stream, rank, ws):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])

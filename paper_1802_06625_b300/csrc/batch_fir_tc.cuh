@@ -16,9 +16,11 @@
 //                on a change of instance, its tap operands are copied in once
 //                the GEMMs of the item before have completed;
 //   warp 16      issues the FIR GEMMs (per shift and K step, hi x [B_hi|B_lo]
-//                and lo x [B_hi|B_lo] as N = 128 GEMMs) into one of four
-//                128-column TMEM accumulators (all 512 columns: the GEMM
-//                time per item varies with T, the read-back's does not), hands the item's record on
+//                as an N = 128 GEMM and lo x B_hi as an N = 64 one: the
+//                lo x lo product, ~2^-22 of the result, is left out) into
+//                one of four 128-column TMEM accumulators (all 512 columns:
+//                the GEMM time per item varies with T, the read-back's does
+//                not), hands the item's record on
 //                with the accumulator, and frees the stage by a commit once
 //                the GEMMs have read it;
 //   warps 8-15   read-back: y = the two column halves added, scaled back by
@@ -243,7 +245,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
             umma_f16(d, ds + 2 * ks, db + 2 * ks, kTIdescN128, (sh > 0 || ks > 0) ? 1u : 0u);
-            umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN128, 1u);
+            umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN64, 1u);  // lo x B_hi only
           }
         }
         umma_commit(smem_u32(&mma_done[i % kBfAccs]));

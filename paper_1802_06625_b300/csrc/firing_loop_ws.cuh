@@ -7,7 +7,8 @@
 //                   checks FIR's firing rule on f0 and copies the raw input
 //                   tile (+ halo) into a 2-stage shared-memory ring with bulk
 //                   asynchronous copies (cp.async.bulk, mbarrier tx counts);
-//   warp 1          MMA: the FIR GEMMs of a tile into one of 4 TMEM slots;
+//   warp 1          MMA: the FIR GEMMs of a tile into one of 4 TMEM slots
+//                   (three split products: hi x hi, hi x lo, lo x hi);
 //   warps 2-5       converter: raw FP32 -> split-FP16 chunk array (the
 //                   permuted K-major 128B-swizzle operand), 2-buffer ring,
 //                   with the tile scaled by the power of two of the
@@ -278,11 +279,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           mbar_arrive(smem_u32(&a_empty[b]));
         } else {
           tc_fence_after();
-          // Per shift and K step, hi x [B_hi | B_lo] and lo x [B_hi | B_lo]
-          // as N = 128 GEMMs (the shift's hi and lo tap operands are adjacent,
-          // one 128-row operand): columns 0-63 collect hi x hi + lo x hi,
-          // 64-127 hi x lo + lo x lo.  Descriptors advance by adding the
-          // byte offset / 16 (all shared addresses are below 2^18 bytes).
+          // Per shift and K step, hi x [B_hi | B_lo] as one N = 128 GEMM
+          // (the shift's hi and lo tap operands are adjacent, one 128-row
+          // operand) and lo x B_hi as an N = 64 GEMM over its first 64 rows:
+          // columns 0-63 collect hi x hi + lo x hi, 64-127 hi x lo.  The
+          // lo x lo product (~2^-22 of the result) is left out, as in every
+          // three-pass split; the issue count is the same either way.
+          // Descriptors advance by adding the byte offset / 16 (all shared
+          // addresses are below 2^18 bytes).
           const uint64_t dah = umma_desc_sw128(smem_u32(aop0 + b * kWsAOpBytes));
           const uint32_t d = tmem + static_cast<uint32_t>(j * 128);
           for (int sh = 0; sh < ns; ++sh) {
@@ -291,7 +295,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
               umma_f16(d, ds + 2 * ks, db + 2 * ks, kTIdescN128, (sh > 0 || ks > 0) ? 1u : 0u);
-              umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN128, 1u);
+              umma_f16(d, ds + dlo + 2 * ks, db + 2 * ks, kTIdescN64, 1u);
             }
           }
           umma_commit(smem_u32(&fir_full[j]));
