@@ -37,11 +37,11 @@ from paper_1802_06625_b300 import synth  # noqa: E402
 
 METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 latency"
 # DRAM bytes (read + write) per frame of the 4096 x 1024 workload, per kernel
-# kind, from one ncu capture of the kernel as it stands (48-frame launch of
-# the warp-specialised loop, dram__bytes_read.sum + dram__bytes_write.sum
-# divided by 48); scaled to a launch by the frames it fires.  Remove an entry
-# when its kernel changes.
-TRAFFIC_PER_FRAME = {}
+# name, from one ncu capture of the kernel as it stands (48-frame launch of
+# the warp-specialised loop: 1611.220 MB read + 812.782 MB written, divided
+# by 48); scaled to a launch by the frames it fires.  Remove an entry when
+# its kernel changes.
+TRAFFIC_PER_FRAME = {"firing_loop_ws_kernel": (1611.220e6 + 812.782e6) / 48}
 UNIT = "Msamples/s"
 # FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
 # FP32 lanes x 2 flop x 2.032 GHz.
@@ -317,8 +317,8 @@ def run_ours(args, w):
                                           "(FP16 has the same nominal rate)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         traffic = args.traffic
-        if traffic is None and kind in TRAFFIC_PER_FRAME and w.name == synth.PLAIN_LARGE.name:
-            traffic = TRAFFIC_PER_FRAME[kind] * frames_per_launch
+        if traffic is None and kind_name(kind) in TRAFFIC_PER_FRAME and w.name == synth.PLAIN_LARGE.name:
+            traffic = TRAFFIC_PER_FRAME[kind_name(kind)] * frames_per_launch
         roof["traffic"] = traffic
         roof["kernel"] = kind_name(kind)
         roof["avg_launch_ms"] = kms / kn
@@ -416,9 +416,21 @@ def run_batched(args, dev, compare_plain=True):
                     "between the launches too"}
     bt_off = list(bt.offsets)
     bt.close()
+    # blocks of the timed frame whose decision lies inside the parity guard
+    # band (|E - tau| <= 1e-3 |tau|, where either decision is correct), by T,
+    # from the FP32 block energies of the CUDA-core FIR (untimed)
+    from paper_1802_06625_b300.graph import fir_energy
+    band = {f"T={t}": 0 for t in sorted({w.T for w in ws_})}
+    for i, w in enumerate(ws_):
+        _, e, _ = fir_energy(x[bt_off[i]:bt_off[i] + w.F * w.B].reshape(1, -1), w.taps(), w.F, w.B, w.T,
+                             want_y=False)
+        band[f"T={w.T}"] += int((torch.abs(e.double() - w.tau) <= 1e-3 * abs(w.tau)).sum())
+    in_band = {**band, "seed": b.seed, "blocks": blocks,
+               "note": "blocks with |E - tau| <= 1e-3 |tau| by the FP32 energies of the CUDA-core FIR"}
     out = {"workload": b.name, "instances": b.instances, "samples_per_step": samples, "launches_per_step": 3,
            "batched_Msamples_s": samples / t_batched / 1e6, "batched_ms_per_step": 1e3 * t_batched,
-           "roofline": roof, "tuning": tuned, "candidates_ms": [round(c["ms"], 4) for c in candidates]}
+           "roofline": roof, "in_band_blocks": in_band, "tuning": tuned,
+           "candidates_ms": [round(c["ms"], 4) for c in candidates]}
     if not compare_plain:
         return out
 
