@@ -132,6 +132,7 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
                            : static_cast<int>(static_cast<int64_t>(bp.fir_tiles) * (blockIdx.x + 1) / gridDim.x);
   const int n = i1 - i0;
   const int B = bp.B, rpb = B / kTR;
+  const int lgB = __ffs(B) - 1;  // B divides the 4096-sample tile and is a multiple of 32: a power of two
 
   if (tid == 0) {
     for (int q = 0; q < 3 * kBfStages + 2 * kBfAccs + 2; ++q) mbar_init(smem_u32(raw_full + q), 1);
@@ -475,14 +476,14 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
         __syncwarp();
       }
       bar256<2>();  // every row energy is in eth
-      const int nb = r.nv / B;
+      const int nb = r.nv >> lgB;
       if (et < nb) {
         float E = 0.f;
         for (int k = 0; k < rpb; ++k) {
           const int c = et * rpb + k;
           E += eth[c] + eth[128 + c];
         }
-        r.energy[r.s0 / B + et] = E;
+        r.energy[(r.s0 >> lgB) + et] = E;
       }
     }
     if (!ok && et == 0) fail(24, 0);

@@ -116,4 +116,20 @@ struct SlotMap {
   __device__ __forceinline__ int64_t slot(int64_t k) const { return (seq0 + k) % cap; }
 };
 
+// The same slot, (seq0 + k) % cap for k >= 0, from a base taken once per
+// launch: one 64-bit modulo up front, then a subtraction per frame (a run
+// fires at most cap frames; the modulo stays for any larger k).
+struct RingSlot {
+  int32_t base, cap;
+  __device__ __forceinline__ static RingSlot of(int64_t seq0, int32_t cap) {
+    return RingSlot{static_cast<int32_t>(seq0 % cap), cap};
+  }
+  __device__ __forceinline__ int32_t at(int k) const {
+    int32_t v = base + k;
+    if (v >= cap) v -= cap;
+    if (v >= cap) v %= cap;
+    return v;
+  }
+};
+
 }  // namespace prune

@@ -134,6 +134,17 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   int sx_pred = 0;  // scale exponent of this pipeline's previous tile
   // barrier of this pipeline's 128 threads (named barrier 1 + pipe)
   auto psync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + pipe) : "memory"); };
+  // B divides the 4096-sample tile and is a multiple of 32: a power of two,
+  // so every division by B or by rows per block is a shift; ring slots take
+  // one 64-bit modulo per launch and a subtraction per tile
+  const int lgB = __ffs(f.B) - 1, lgR = lgB - 5;
+  const RingSlot fring = RingSlot::of(f.yslot.seq0, p.C);   // frame slot of the look-back words
+  const RingSlot rring = RingSlot::of(p.rslot.seq0, p.rslot.cap);
+  const RingSlot ering = f.energy ? RingSlot::of(f.eslot.seq0, f.eslot.cap) : RingSlot{0, 1};
+  const RingSlot sring = f.src.ring ? RingSlot::of(f.src.seq0, f.src.cap) : RingSlot{0, 1};
+  auto frame_at = [&](int k) -> const float2 * {
+    return f.src.ring ? f.src.ring[sring.at(k)] : f.src.base + static_cast<int64_t>(k) * f.src.stride;
+  };
 
   // constant operands, once per CTA
   {
@@ -205,7 +216,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           const int64_t s0n = static_cast<int64_t>(tn) * kTTile;
           const int64_t lo = s0n >= static_cast<int64_t>(S) * kTR ? s0n - static_cast<int64_t>(S) * kTR : 0;
           const int64_t hi = min(s0n + static_cast<int64_t>(kTTile), f.L);
-          pf_src = f.src.frame(kn) + lo;  // issued later, while warps 1-3 idle in the look-back
+          pf_src = frame_at(kn) + lo;  // issued later, while warps 1-3 idle in the look-back
           pf_bytes = static_cast<uint32_t>((hi - lo) * 8);
         }
       }
@@ -230,8 +241,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     // tile is scaled by the pipeline's previous tile's power of two; its
     // largest component (halo included), gathered on the way, checks that
     // scale after the barrier, and a tile it does not fit is converted again.
-    const float2 *cur = f.src.frame(k);
-    const float2 *prev = k > 0 ? f.src.frame(k - 1) : nullptr;
+    const float2 *cur = frame_at(k);
+    const float2 *prev = k > 0 ? frame_at(k - 1) : nullptr;
     auto load_piece = [&](int q, float (&v)[8]) {
       const int row = q >> 3, pc = q & 7;
       const int j = 16 * (row & 7) + (row >> 3) - S;
@@ -381,13 +392,13 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     // block energies: eth is ordered by chunk; block b owns [rpb b, rpb (b+1));
     // a shuffle tree per segment of the warp, in a fixed order
     const int rpb = f.B / kTR;  // rows (chunks) per block
-    const int nb = nv / f.B;
+    const int nb = nv >> lgB;
     {
       float v = eth[tid];
       const int seg = rpb < 32 ? rpb : 32;
       for (int off = seg >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (rpb <= 32) {
-        if ((tid & (seg - 1)) == 0 && tid / rpb < nb) Et[tid / rpb] = v;
+        if ((tid & (seg - 1)) == 0 && (tid >> lgR) < nb) Et[tid >> lgR] = v;
       } else {
         if (lane == 0) red4[warp] = v;
       }
@@ -398,7 +409,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
         Et[tid] = E;
       }
       psync();
-      if (f.energy && tid < nb) f.energy[f.eslot.slot(k) * f.F + s0 / f.B + tid] = Et[tid];
+      if (f.energy && tid < nb) f.energy[static_cast<int64_t>(ering.at(k)) * f.F + tile * (kTTile >> lgB) + tid] = Et[tid];
     }
     // ---- SEL inside the tile: stable ballot compaction
     if (warp == 0) {
@@ -419,8 +430,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
     // time, and scaled by 2^m
     {
       const float hsc = exp2i(tp.m);
-      const int rk = jc < rows_valid ? s_rank[jc / rpb] : -1;
-      const int hrow = rk * rpb + jc % rpb;
+      const int rk = jc < rows_valid ? s_rank[jc >> lgR] : -1;
+      const int hrow = rk * rpb + (jc & (rpb - 1));
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float y[32];
@@ -465,7 +476,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
       hx_pending = true;
     }
     // ... while one warp runs the look-back for the tile's offset in the frame
-    const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
+    const int64_t fslot = fring.at(k);
     if (warp == 0) {
       const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt, seq, lane);
       if (lane == 0) *s_prefix = pr;
@@ -484,8 +495,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
       failed = true;
       break;
     }
-    const int64_t rs = p.rslot.slot(k);
-    if (tid < nb && s_rank[tid] >= 0) p.rec_idx[rs * f.F + prefix + s_rank[tid]] = static_cast<int32_t>(s0 / f.B) + tid;
+    const int64_t rs = rring.at(k);
+    if (tid < nb && s_rank[tid] >= 0) p.rec_idx[rs * f.F + prefix + s_rank[tid]] = tile * (kTTile >> lgB) + tid;
 
     // ---- SINK payload: HX_b outputs at their compacted positions
     if (cnt > 0) {
@@ -515,8 +526,8 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           tmem_ld_wait();
         }
         if (m < cnt * rpb) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
-          float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + m / rpb) * f.B +
-                                                 (m % rpb) * kTR + hf * 16);
+          float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + (m >> lgR)) * f.B +
+                                                 (m & (rpb - 1)) * kTR + hf * 16);
           if (f2 != 1.f)  // a scale beyond one float factor (uniform, rare)
             for (int i = 0; i < 32; ++i) o[i] *= f2;
 #pragma unroll

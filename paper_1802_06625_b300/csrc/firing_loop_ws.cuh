@@ -447,6 +447,13 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     const int bar = 2 + e;
     auto gsync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory"); };
     const int rpb = f.B / kTR;
+    // B divides the 4096-sample tile and is a multiple of 32: a power of
+    // two, so every division by B or by rows per block is a shift; ring
+    // slots take one 64-bit modulo per launch and a subtraction per tile
+    const int lgB = __ffs(f.B) - 1, lgR = lgB - 5;
+    const RingSlot fring = RingSlot::of(f.yslot.seq0, p.C);   // frame slot of the look-back words
+    const RingSlot rring = RingSlot::of(p.rslot.seq0, p.rslot.cap);
+    const RingSlot ering = f.energy ? RingSlot::of(f.eslot.seq0, f.eslot.cap) : RingSlot{0, 1};
     constexpr int kHxIssuer = 96;               // lane 0 of the group's last warp
     bool hx_issued = false;
     for (uint32_t i = static_cast<uint32_t>(e);; i += kWsGroups) {
@@ -460,7 +467,6 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       tc_fence_after();
       const int k = it.k, tile = it.tile, nv = it.nv;
       const uint64_t seq = static_cast<uint64_t>(f.yslot.seq0) + k;
-      const int64_t s0 = static_cast<int64_t>(tile) * kTTile;
       const int rows_valid = nv / kTR;
       const uint32_t slot = tmem + static_cast<uint32_t>(j * 128);
       // ---- FIR rows = columns 0-63 + columns 64-127 (y 2^(sx + s_taps));
@@ -516,7 +522,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       }
       // ---- block energies (fixed order), DET and SEL on the first warp: a
       //      lane sums 4 rows, the lanes of a block combine by an xor tree
-      const int nb = nv / f.B;
+      const int nb = nv >> lgB;
       int cnt_w0 = 0;  // warp 0: selected blocks, known before the look-back
       if (gw == 0) {
         const float4 e4 = reinterpret_cast<const float4 *>(G.eth)[lane];  // rows 4 lane .. 4 lane + 3
@@ -533,7 +539,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           reinterpret_cast<float4 *>(G.Et)[lane] = e4;
         }
         __syncwarp();
-        const int64_t eb = f.energy ? f.eslot.slot(k) * f.F + s0 / f.B : 0;
+        const int64_t eb = f.energy ? static_cast<int64_t>(ering.at(k)) * f.F + tile * (kTTile >> lgB) : 0;
         for (int b0 = 0; b0 < nb; b0 += 32) {
           const int b = b0 + lane;
           const float E = b < nb ? G.Et[b] : 0.f;
@@ -546,7 +552,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         if (lane == 0) G.cnt = cnt_w0;
       }
       // ---- look-back for the tile's offset in the frame (overlaps the GEMM)
-      const int64_t fslot = static_cast<int64_t>(seq % static_cast<uint64_t>(p.C));
+      const int64_t fslot = fring.at(k);
       if (gw == 0) {
         const int64_t pr = lookback_warp(p, p.look + fslot * f.tiles, tile, seq + 1, cnt_w0, seq, lane);
         if (lane == 0) G.prefix = pr;
@@ -562,14 +568,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         if (gt == 0) *stop = 1;
         break;
       }
-      const int64_t rs = p.rslot.slot(k);
-      if (gt < nb && G.rank[gt] >= 0) p.rec_idx[rs * f.F + prefix + G.rank[gt]] = static_cast<int32_t>(s0 / f.B) + gt;
+      const int64_t rs = rring.at(k);
+      if (gt < nb && G.rank[gt] >= 0) p.rec_idx[rs * f.F + prefix + G.rank[gt]] = tile * (kTTile >> lgB) + gt;
       // ---- SINK payload: the selected rows at their compacted places (the
       //      wait outcomes are combined at the completion barrier below)
       const bool okh = ws_wait(smem_u32(&hx_full[j]), use & 1u, p.timeout_ns, stop);
       tc_fence_after();
       if (okh && cnt > 0) {
-        const int rk = jc < rows_valid ? G.rank[jc / rpb] : -1;
+        const int rk = jc < rows_valid ? G.rank[jc >> lgR] : -1;
         float f1, f2;  // HX outputs are H y 2^(sx + s_taps + m + s_h)
         pow2_pair(-(it.sx + tp.s_taps + tp.m + tp.s_h), f1, f2);
 #pragma unroll 1
@@ -582,7 +588,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
             for (int q = 0; q < 32; ++q) o[q] *= f2;
           }
           if (rk >= 0) {  // 32-byte stores (whole sectors; the half-row starts 128-byte aligned)
-            float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc % rpb) * kTR +
+            float *dst = reinterpret_cast<float *>(p.rec_y + rs * f.L + (prefix + rk) * f.B + (jc & (rpb - 1)) * kTR +
                                                    hf * 16);
 #pragma unroll
             for (int q = 0; q < 4; ++q) st_global_v8(dst + 8 * q, o + 8 * q, f1);
