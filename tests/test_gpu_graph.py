@@ -362,3 +362,24 @@ def test_staging_and_fir_rings_are_allocated_only_when_needed(G):
     g.push(x)
     assert g.run(sync=True) == 2
     g.close()
+
+
+@pytest.mark.parametrize("T,kind", [(64, "ws"), (100, "pipes")])
+def test_ring_slots_wrap_inside_runs(G, T, kind):
+    # C = 5 look-back/frame slots and a 7-frame record ring, fired 3 frames
+    # per run for 15 frames: runs start at frame slots 0, 3, 1, 4, 2 and
+    # record slots 0, 3, 6, 2, 5, so both rings wrap inside runs; every
+    # frame against the oracle on the whole stream.
+    w = synth.PlainWorkload("wrap", F=40, B=256, T=T, N=32, frames=15, tau=1024.0, seed=T + 5, p=0.4, C=5)
+    x = w.frames_tensor(0, 15)
+    g = G.Graph(w.F, w.B, w.T, w.N, w.tau, w.taps(), w.H(), C=5, out_frames=7)
+    g.profile(True)
+    xd = x.cuda()
+    recs = []
+    for k in range(0, 15, 3):
+        g.push(xd[k:k + 3])
+        assert g.run(sync=True) == 3
+        recs += g.pull()
+    assert g.kernel_times(g.KIND_LOOP_TC)[1] == 5, "the tensor-core loop did not fire every run"
+    g.close()
+    check_against_oracle(w, x.numpy(), recs)
