@@ -439,13 +439,12 @@ static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(Batc
           const int m = q >> 4, cc = q & 15;
           float v[8] = {u[k][0].x, u[k][0].y, u[k][0].z, u[k][0].w, u[k][1].x, u[k][1].y, u[k][1].z, u[k][1].w};
           // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[e] *= sc;
+          const float2 s2 = make_float2(sc, sc);
           uint4 h4, l4;
-          split_pair(v[0], v[1], h4.x, l4.x);
-          split_pair(v[2], v[3], h4.y, l4.y);
-          split_pair(v[4], v[5], h4.z, l4.z);
-          split_pair(v[6], v[7], h4.w, l4.w);
+          split_pair2(__fmul2_rn(make_float2(v[0], v[1]), s2), h4.x, l4.x);
+          split_pair2(__fmul2_rn(make_float2(v[2], v[3]), s2), h4.y, l4.y);
+          split_pair2(__fmul2_rn(make_float2(v[4], v[5]), s2), h4.z, l4.z);
+          split_pair2(__fmul2_rn(make_float2(v[6], v[7]), s2), h4.w, l4.w);
           hmax_abs_acc(hm, h4.x);
           hmax_abs_acc(hm, h4.y);
           hmax_abs_acc(hm, h4.z);

@@ -336,15 +336,14 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
           if (q < npieces) {
             const int row = q >> 3, pc = q & 7;
             const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
-            float4 a = u[k][0], c = u[k][1];
+            const float4 a = u[k][0], c = u[k][1];
             // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
-            a.x *= xsc; a.y *= xsc; a.z *= xsc; a.w *= xsc;
-            c.x *= xsc; c.y *= xsc; c.z *= xsc; c.w *= xsc;
+            const float2 x2 = make_float2(xsc, xsc);
             uint4 h4, l4;
-            split_pair(a.x, a.y, h4.x, l4.x);
-            split_pair(a.z, a.w, h4.y, l4.y);
-            split_pair(c.x, c.y, h4.z, l4.z);
-            split_pair(c.z, c.w, h4.w, l4.w);
+            split_pair2(__fmul2_rn(make_float2(a.x, a.y), x2), h4.x, l4.x);
+            split_pair2(__fmul2_rn(make_float2(a.z, a.w), x2), h4.y, l4.y);
+            split_pair2(__fmul2_rn(make_float2(c.x, c.y), x2), h4.z, l4.z);
+            split_pair2(__fmul2_rn(make_float2(c.z, c.w), x2), h4.w, l4.w);
             hmax_abs_acc(hm, h4.x);
             hmax_abs_acc(hm, h4.y);
             hmax_abs_acc(hm, h4.z);
@@ -440,16 +439,24 @@ static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(Batc
       float f1, f2;
       pow2_pair(-(r.sx + r.s_taps), f1, f2);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] += w[q];
+      for (int q = 0; q < 32; q += 2) {
+        const float2 s = __fadd2_rn(make_float2(v[q], v[q + 1]), make_float2(w[q], w[q + 1]));
+        v[q] = s.x;
+        v[q + 1] = s.y;
+      }
       if (f2 != 1.f) {  // a scale beyond one float factor (uniform, rare)
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] *= f2;
       }
+      float2 e2 = make_float2(0.f, 0.f);  // even and odd columns' squares
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        v[q] *= f1;
-        e = fmaf(v[q], v[q], e);
+      for (int q = 0; q < 32; q += 2) {
+        const float2 s = __fmul2_rn(make_float2(v[q], v[q + 1]), make_float2(f1, f1));
+        v[q] = s.x;
+        v[q + 1] = s.y;
+        e2 = __ffma2_rn(s, s, e2);
       }
+      e = e2.x + e2.y;
       // the accumulator is free once every thread has its rows
       tc_fence_before();
       bar256<2>();

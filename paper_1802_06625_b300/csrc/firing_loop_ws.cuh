@@ -366,15 +366,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           for (int r = 0; r < kWsConvBatch; ++r) {
             const int q = q0 + 128 * r;
             if (q < npieces) {
-              u[r][0].x *= xsc; u[r][0].y *= xsc; u[r][0].z *= xsc; u[r][0].w *= xsc;
-              u[r][1].x *= xsc; u[r][1].y *= xsc; u[r][1].z *= xsc; u[r][1].w *= xsc;
+              const float2 x2 = make_float2(xsc, xsc);
               const int row = q >> 3, pc = q & 7;
               const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
               uint4 h4, l4;
-              split_pair(u[r][0].x, u[r][0].y, h4.x, l4.x);
-              split_pair(u[r][0].z, u[r][0].w, h4.y, l4.y);
-              split_pair(u[r][1].x, u[r][1].y, h4.z, l4.z);
-              split_pair(u[r][1].z, u[r][1].w, h4.w, l4.w);
+              split_pair2(__fmul2_rn(make_float2(u[r][0].x, u[r][0].y), x2), h4.x, l4.x);
+              split_pair2(__fmul2_rn(make_float2(u[r][0].z, u[r][0].w), x2), h4.y, l4.y);
+              split_pair2(__fmul2_rn(make_float2(u[r][1].x, u[r][1].y), x2), h4.z, l4.z);
+              split_pair2(__fmul2_rn(make_float2(u[r][1].z, u[r][1].w), x2), h4.w, l4.w);
               hmax_abs_acc(hm, h4.x);
               hmax_abs_acc(hm, h4.y);
               hmax_abs_acc(hm, h4.z);
@@ -475,7 +474,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       //      the first 8, lo in the next 8, two FP16 per column)
       if (okf && it.t != kSentinel) {
         const float hsc = exp2i(tp.m);
-        float en = 0.f;
+        const float2 hsc2 = make_float2(hsc, hsc);
+        float2 en2 = make_float2(0.f, 0.f);  // even and odd columns' squares
 #pragma unroll 1
         for (int qd = 0; qd < 4; ++qd) {
           float v[16], w[16];
@@ -485,15 +485,14 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           uint32_t hi[8], lo[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const float y0 = v[2 * q] + w[2 * q], y1 = v[2 * q + 1] + w[2 * q + 1];
-            en = fmaf(y0, y0, en);
-            en = fmaf(y1, y1, en);
-            split_pair(y0 * hsc, y1 * hsc, hi[q], lo[q]);
+            const float2 y = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), make_float2(w[2 * q], w[2 * q + 1]));
+            en2 = __ffma2_rn(y, y, en2);
+            split_pair2(__fmul2_rn(y, hsc2), hi[q], lo[q]);
           }
           tmem_st8(slot + tlane + static_cast<uint32_t>(64 + 16 * qd), hi);
           tmem_st8(slot + tlane + static_cast<uint32_t>(72 + 16 * qd), lo);
         }
-        G.eth[jc] = jc < rows_valid ? mul_pow2(en, -2 * (it.sx + tp.s_taps)) : 0.f;
+        G.eth[jc] = jc < rows_valid ? mul_pow2(en2.x + en2.y, -2 * (it.sx + tp.s_taps)) : 0.f;
         tmem_st_wait();
       }
       tc_fence_before();

@@ -165,10 +165,25 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-// Eight scaled floats as one 32-byte global store (address 32-byte aligned).
+// The same split of two components with packed FP32 arithmetic: lo = x - hi
+// as one two-wide FMA (exact: x - hi is the low 13 bits of x).
+__device__ __forceinline__ void split_pair2(float2 v, uint32_t &hi, uint32_t &lo) {
+  const float2 h = make_float2(__uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u),
+                               __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u));
+  const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), v);
+  const __half2 hh = __floats2half2_rn(h.x, h.y), ll = __floats2half2_rn(l.x, l.y);
+  hi = *reinterpret_cast<const uint32_t *>(&hh);
+  lo = *reinterpret_cast<const uint32_t *>(&ll);
+}
+
+// Eight scaled floats as one 32-byte global store (address 32-byte aligned);
+// the scaling as four two-wide multiplies.
 __device__ __forceinline__ void st_global_v8(float *dst, const float *v, float sc) {
-  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(v[0] * sc), "f"(v[1] * sc),
-               "f"(v[2] * sc), "f"(v[3] * sc), "f"(v[4] * sc), "f"(v[5] * sc), "f"(v[6] * sc), "f"(v[7] * sc)
+  const float2 s2 = make_float2(sc, sc);
+  const float2 a = __fmul2_rn(make_float2(v[0], v[1]), s2), b = __fmul2_rn(make_float2(v[2], v[3]), s2);
+  const float2 c = __fmul2_rn(make_float2(v[4], v[5]), s2), d = __fmul2_rn(make_float2(v[6], v[7]), s2);
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "f"(a.x), "f"(a.y), "f"(b.x),
+               "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
                : "memory");
 }
 
