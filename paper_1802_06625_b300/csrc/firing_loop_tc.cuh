@@ -297,15 +297,14 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
           const int q = q0 + tid + kTPipeThreads * i;
           if (q >= npieces) continue;
           // scaled by 2^sxc (a multiply by 1 for 2^0: one instantiation keeps the code small)
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[i][e] *= xsc;
+          const float2 x2 = make_float2(xsc, xsc);
           const int row = q >> 3, pc = q & 7;
           const uint32_t off = static_cast<uint32_t>(row) * 128u + (static_cast<uint32_t>(pc ^ (row & 7)) << 4);
           uint4 h4, l4;
-          split_pair(v[i][0], v[i][1], h4.x, l4.x);
-          split_pair(v[i][2], v[i][3], h4.y, l4.y);
-          split_pair(v[i][4], v[i][5], h4.z, l4.z);
-          split_pair(v[i][6], v[i][7], h4.w, l4.w);
+          split_pair2(__fmul2_rn(make_float2(v[i][0], v[i][1]), x2), h4.x, l4.x);
+          split_pair2(__fmul2_rn(make_float2(v[i][2], v[i][3]), x2), h4.y, l4.y);
+          split_pair2(__fmul2_rn(make_float2(v[i][4], v[i][5]), x2), h4.z, l4.z);
+          split_pair2(__fmul2_rn(make_float2(v[i][6], v[i][7]), x2), h4.w, l4.w);
           hmax_abs_acc(hm, h4.x);
           hmax_abs_acc(hm, h4.y);
           hmax_abs_acc(hm, h4.z);
@@ -377,16 +376,19 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
 
     // ---- DET: energy of chunk jc (GEMM row m), both column halves
     {
-      float e = 0.f;
+      float2 e2 = make_float2(0.f, 0.f);  // even and odd columns' squares
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         float t16[16];
         tmem_ld16(tmem + tlane + static_cast<uint32_t>(h * 16), t16);
         tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) e = fmaf(t16[i], t16[i], e);
+        for (int i = 0; i < 16; i += 2) {
+          const float2 t = make_float2(t16[i], t16[i + 1]);
+          e2 = __ffma2_rn(t, t, e2);
+        }
       }
-      eth[jc] = jc < rows_valid ? mul_pow2(e, -2 * (sx + tp.s_taps)) : 0.f;
+      eth[jc] = jc < rows_valid ? mul_pow2(e2.x + e2.y, -2 * (sx + tp.s_taps)) : 0.f;
     }
     psync();
     // block energies: eth is ordered by chunk; block b owns [rpb b, rpb (b+1));
