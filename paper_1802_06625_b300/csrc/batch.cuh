@@ -198,8 +198,7 @@ struct BhxRec {
 
 static __global__ void __launch_bounds__(kBhxThreads, 1) batch_hx_tc_kernel(BatchParams bp) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *base = smem_align1024(smem_raw);
   unsigned char *b_hi = base, *b_lo = base + kTcOpBytes;
   unsigned char *stage0 = base + 2 * kTcOpBytes;  // stage k: rows (fp32), then in place A hi | A lo
   unsigned char *misc = stage0 + 2 * kBhxStageBytes;

@@ -101,8 +101,7 @@ static_assert(sizeof(BfRec) <= 80, "the misc layout holds 3 + 4 records of at mo
 
 static __global__ void __launch_bounds__(kBfThreads, 1) batch_fir_tc_kernel(BatchParams bp) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *base = smem_align1024(smem_raw);
   unsigned char *bops = base;                       // tap operands of the loaded instance (shift s: hi, lo)
   // stage k: the raw tile (sample s0 - kBfRawHalo at byte 0), then in place
   // the chunk array: hi (16 + S groups of 1024 bytes), then lo

@@ -106,8 +106,7 @@ static __global__ void __launch_bounds__(NP * kTPipeThreads, 1) firing_loop_tc_k
   const LoopParams &p = tp.lp;
   const FirParams &f = p.f;
   const int ns = tp.ns, S = ns - 1;
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *base = smem_align1024(smem_raw);
   unsigned char *bfir = base;
   unsigned char *bhx = bfir + ns * 2 * kTOpBytes;
   const int cta_tid = threadIdx.x, cta_warp = cta_tid >> 5;

@@ -79,6 +79,14 @@ __host__ inline cudaError_t hx_tc_prepare_b(const float2 *H, int N, int sh, cons
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// The dynamic shared memory base rounded up to a 1024-byte boundary (the
+// 128-byte-swizzle operands need it) by pointer arithmetic on the shared
+// array itself: pointers derived from it stay shared-memory pointers, so
+// accesses through them are shared-memory accesses, not generic ones (a
+// round trip through an integer hides the address space from the compiler).
+__device__ __forceinline__ unsigned char *smem_align1024(unsigned char *p) {
+  return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
+}
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), LBO unused for this layout (1), descriptor
@@ -179,8 +187,7 @@ struct HxTcParams {
 static __global__ void __launch_bounds__(kTcThreads, 1) hx_tc_kernel(HxTcParams tp) {
   extern __shared__ unsigned char smem_raw[];
   const HxParams &p = tp.p;
-  unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                          ~static_cast<uintptr_t>(1023));
+  unsigned char *base = smem_align1024(smem_raw);
   unsigned char *a_hi = base, *a_lo = base + kTcOpBytes;
   unsigned char *b_hi = base + 2 * kTcOpBytes, *b_lo = base + 3 * kTcOpBytes;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 4 * kTcOpBytes);
