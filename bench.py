@@ -38,10 +38,10 @@ from paper_1802_06625_b300 import synth  # noqa: E402
 METRIC = "graph Msamples/s + % HBM roofline on 1 B300, batched vs plain; p99 latency"
 # DRAM bytes (read + write) per frame of the 4096 x 1024 workload, per kernel
 # name, from one ncu capture of the kernel as it stands (48-frame launch of
-# the warp-specialised loop: 1611.216 MB read + 813.465 MB written, divided
+# the warp-specialised loop: 1611.218 MB read + 813.758 MB written, divided
 # by 48); scaled to a launch by the frames it fires.  Remove an entry when
 # its kernel changes.
-TRAFFIC_PER_FRAME = {"firing_loop_ws_kernel": (1611.216e6 + 813.465e6) / 48}
+TRAFFIC_PER_FRAME = {"firing_loop_ws_kernel": (1611.218e6 + 813.758e6) / 48}
 UNIT = "Msamples/s"
 # FP32 FFMA peak from the unit counts and clock of the part: 148 SMs x 128
 # FP32 lanes x 2 flop x 2.032 GHz.

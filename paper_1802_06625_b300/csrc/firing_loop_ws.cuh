@@ -9,14 +9,14 @@
 //                   asynchronous copies (cp.async.bulk, mbarrier tx counts);
 //   warp 1          MMA: the FIR GEMMs of a tile into one of 4 TMEM slots
 //                   (three split products: hi x hi, hi x lo, lo x hi);
-//   warps 2-5       converter: raw FP32 -> split-FP16 chunk array (the
+//   warps 2-7       converter: raw FP32 -> split-FP16 chunk array (the
 //                   permuted K-major 128B-swizzle operand), 2-buffer ring,
 //                   with the tile scaled by the power of two of the
 //                   converter's previous tile; the tile's largest component
 //                   (halo included), gathered from the same registers, checks
 //                   that scale after the converter's barrier, and the rare
 //                   tile it does not fit is converted again with its own;
-//   warps 6-17      three epilogue groups, tiles taken round-robin: block
+//   warps 8-19      three epilogue groups, tiles taken round-robin: block
 //                   energies, DET and SEL, the HX_b operand written back into
 //                   the slot's free TMEM columns (two FP16 per column), HX_b as
 //                   a GEMM with its A operand in tensor memory on all 128 rows
@@ -40,8 +40,13 @@
 
 namespace prune {
 
-constexpr int kWsWarps = 18;
-constexpr int kWsThreads = kWsWarps * 32;     // 576
+// Six converter warps: the converter sets the tile period, and six measured
+// faster than four (five did not); 640 threads at 90 registers fit the file.
+constexpr int kWsConvWarps = 6;              // converter warps (2 .. 1 + kWsConvWarps)
+constexpr int kWsConvThreads = kWsConvWarps * 32;
+constexpr int kWsEpiWarp0 = 2 + kWsConvWarps; // first epilogue warp
+constexpr int kWsWarps = kWsEpiWarp0 + 12;
+constexpr int kWsThreads = kWsWarps * 32;
 constexpr int kWsGroups = 3;                  // epilogue groups
 constexpr int kWsSlots = 4;                   // TMEM slots of 128 columns
 constexpr int kWsRawHalo = 64;                // halo samples staged (S <= 2)
@@ -80,7 +85,7 @@ struct WsGroup {
 constexpr uint32_t kWsGroupOff = 1024;
 static_assert(kWsGroupOff + kWsGroups * sizeof(WsGroup) <= kWsMiscBytes, "the groups' scratch fits the misc region");
 static_assert(24 * sizeof(uint64_t) <= 256, "the mbarriers fit [0, 256)");
-static_assert(528 + 24 * sizeof(uint32_t) <= kWsGroupOff, "the converter's maxima fit [528, 1024)");
+static_assert(528 + 2 * 3 * kWsConvWarps * sizeof(uint32_t) <= kWsGroupOff, "the converter's maxima fit [528, 1024)");
 static_assert(8 * sizeof(WsItem) <= 192, "the item records fit [256, 448)");
 
 // Cold paths.  They stay inlined: as calls, the register saves around them
@@ -138,7 +143,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
   WsItem *item_slot = item_a + 2;                                   // [4]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(misc + 512);
   volatile int32_t *stop = reinterpret_cast<volatile int32_t *>(misc + 520);
-  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 528);         // [2][3][4] converter warps' maxima
+  uint32_t *cred = reinterpret_cast<uint32_t *>(misc + 528);         // [2][3][kWsConvWarps] converter warps' maxima
   WsGroup *grp = reinterpret_cast<WsGroup *>(misc + kWsGroupOff);   // [3]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned long long total = static_cast<unsigned long long>(f.frames) * f.tiles;
@@ -309,9 +314,9 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       umma_commit(smem_u32(&fin[0]));
       mbar_wait_bounded(smem_u32(&fin[0]), 0u, p.timeout_ns);
     }
-  } else if (warp < 6) {
+  } else if (warp < kWsEpiWarp0) {
     // ================================================================ converter
-    const int ct = tid - 64;  // 0..127
+    const int ct = tid - 64;  // 0 .. kWsConvThreads - 1
     int sentinels = 0;
     int sx_pred = 0;          // scale exponent of this converter's previous tile
     for (uint32_t i = 0; sentinels < kWsGroups; ++i) {
@@ -328,9 +333,9 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       unsigned char *ahi = aop0 + b * kWsAOpBytes;
       unsigned char *alo = ahi + (kTGroups + S) * 1024;
       const int npieces = (kTGroups + S) * 64;
-      // cred: [item parity][hi max, FP32 max, spare][4 warps]: no thread
+      // cred: [item parity][hi max, FP32 max, spare][converter warp]: no thread
       // rewrites a buffer that another may still read
-      uint32_t *cr = cred + (i & 1u) * 12u;
+      uint32_t *cr = cred + (i & 1u) * (3u * kWsConvWarps);
       // kWsConvBatch pieces per thread at a time: all their loads are
       // issued before the first split, so the load latency is paid once per
       // batch.  The pieces are scaled by 2^sx (a multiply by 1 for 2^0: one
@@ -340,11 +345,11 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
       auto convert = [&](int sxc) -> uint32_t {
         const float xsc = exp2i(sxc);
         uint32_t hm = 0u;
-        for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * 128) {
+        for (int q0 = ct; q0 < npieces; q0 += kWsConvBatch * kWsConvThreads) {
           float4 u[kWsConvBatch][2];
 #pragma unroll
           for (int r = 0; r < kWsConvBatch; ++r) {
-            const int q = q0 + 128 * r;
+            const int q = q0 + kWsConvThreads * r;
             const int row = q >> 3, pc = q & 7;
             const int j = 16 * (row & 7) + (row >> 3) - S;  // chunk from the tile start (>= -S)
             if (q < npieces && kTR * j + 4 * pc < it.nv) {
@@ -363,7 +368,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
           }
 #pragma unroll
           for (int r = 0; r < kWsConvBatch; ++r) {
-            const int q = q0 + 128 * r;
+            const int q = q0 + kWsConvThreads * r;
             if (q < npieces) {
               const float2 x2 = make_float2(xsc, xsc);
               const int row = q >> 3, pc = q & 7;
@@ -393,7 +398,7 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         if (lane == 0) cr[warp - 2] = wm;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      if (!bar_and(1, 128, okw)) {
+      if (!bar_and(1, kWsConvThreads, okw)) {
         if (ct == 0) fail(kActFir, okr ? 14 : 13, 0);
         break;
       }
@@ -402,25 +407,31 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
         // own exponent differs from the prediction is converted once more
         // (uniform, rare): the exponent a tile is fired with depends on the
         // tile alone, never on the prediction
-        int own = tc_shift_from_hi(max(max(cr[0], cr[1]), max(cr[2], cr[3])), sx);
+        uint32_t hmx = cr[0];
+#pragma unroll
+        for (int w = 1; w < kWsConvWarps; ++w) hmx = max(hmx, cr[w]);
+        int own = tc_shift_from_hi(hmx, sx);
         if (own == -1000) {  // zero, subnormal or inf hi parts: the FP32 maximum decides
           const int halo = S * kTR;
           const float4 *w4 = reinterpret_cast<const float4 *>(raw + (kWsRawHalo - halo) * 8);
           float mx = 0.f;
-          for (int q = ct; q < (halo + it.nv) / 2; q += 128) {
+          for (int q = ct; q < (halo + it.nv) / 2; q += kWsConvThreads) {
             const float4 a = w4[q];
             mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
           }
           const uint32_t fm = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-          if (lane == 0) cr[4 + warp - 2] = fm;
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          own = tc_shift_bits(max(max(cr[4], cr[5]), max(cr[6], cr[7])));
+          if (lane == 0) cr[kWsConvWarps + warp - 2] = fm;
+          asm volatile("bar.sync 1, %0;" ::"n"(kWsConvThreads) : "memory");
+          uint32_t fmx = cr[kWsConvWarps];
+#pragma unroll
+          for (int w = 1; w < kWsConvWarps; ++w) fmx = max(fmx, cr[kWsConvWarps + w]);
+          own = tc_shift_bits(fmx);
         }
         if (own != sx) {
           sx = own;
           convert(sx);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+          asm volatile("bar.sync 1, %0;" ::"n"(kWsConvThreads) : "memory");
         }
         it.sx = sx;
         sx_pred = sx;
@@ -434,8 +445,8 @@ static __global__ void __launch_bounds__(kWsThreads, 1) firing_loop_ws_kernel(Tc
     }
   } else {
     // ================================================================ epilogue
-    const int e = (warp - 6) >> 2;              // group 0..2
-    const int gt = tid - 192 - 128 * e;         // 0..127
+    const int e = (warp - kWsEpiWarp0) >> 2;    // group 0..2
+    const int gt = tid - 32 * kWsEpiWarp0 - 128 * e;  // 0..127
     const int gw = gt >> 5;                     // warp within the group
     const int q4 = warp & 3;                    // TMEM lane quarter of this warp
     const int m = q4 * 32 + lane;               // GEMM row (TMEM lane) owned by this thread
