@@ -121,10 +121,10 @@ struct SlotMap {
 // fires at most cap frames; the modulo stays for any larger k).
 struct RingSlot {
   int32_t base, cap;
-  __device__ __forceinline__ static RingSlot of(int64_t seq0, int32_t cap) {
+  __host__ __device__ __forceinline__ static RingSlot of(int64_t seq0, int32_t cap) {
     return RingSlot{static_cast<int32_t>(seq0 % cap), cap};
   }
-  __device__ __forceinline__ int32_t at(int k) const {
+  __host__ __device__ __forceinline__ int32_t at(int k) const {
     int32_t v = base + k;
     if (v >= cap) v -= cap;
     if (v >= cap) v %= cap;

@@ -1,5 +1,7 @@
-"""The fused loops' ticket -> (frame, tile) mapping (tc_ticket_tile) on the
-CPU, compiled from the library's own header with nvcc as host code."""
+"""The fused loops' index arithmetic on the CPU, compiled from the library's
+own headers with nvcc as host code: the ticket -> (frame, tile) mapping
+(tc_ticket_tile) and the ring slots taken from a per-launch base
+(RingSlot)."""
 import os
 import shutil
 import subprocess
@@ -27,3 +29,16 @@ def test_ticket_mapping_is_a_bijection_onto_frames_and_tiles(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.split().count("ok") == 2, r.stdout
+
+
+def test_ring_slot_equals_the_modulo(tmp_path):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    exe = tmp_path / "ring_slot_check"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O1", "-I", CSRC, "-I",
+                    os.path.join(HERE, "..", "include"), "-DPRUNE_BUILD", os.path.join(HERE, "native", "ring_slot_check.cu"),
+                    "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok"), r.stdout
